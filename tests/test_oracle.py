@@ -1,0 +1,314 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a brute-force
+definition, numpy's FFT, a closed-form solution of the GPE, an exact invariance
+of the splitting, or numbers printed in the paper (tests/golden/).  Together
+they fail on a dropped factor, a wrong sign, a transposed axis or a wrong
+normalisation anywhere in the oracle.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import gpe_inputs as gi
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+# --------------------------------------------------------------------- FFT
+@pytest.mark.parametrize("n", [(1,), (2,), (4,), (8,), (16,), (32,), (64,),
+                               (8, 4), (2, 16), (16, 16), (4, 2, 8), (8, 8, 4), (2, 2, 2)])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_fft_matches_bruteforce_dft(orc, n, sign):
+    rng = np.random.default_rng(sum(n) + sign)
+    N = int(np.prod(n))
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    assert rel(orc.fft(x, n, sign), orc.dft_brute(x, n, sign)) < 1e-13
+
+
+@pytest.mark.parametrize("n", [(256,), (4096,), (128, 64), (32, 16, 8)])
+def test_fft_matches_numpy(orc, n):
+    rng = np.random.default_rng(7)
+    shape = tuple(reversed(n))
+    x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    assert rel(orc.fft(x, n, -1), np.fft.fftn(x)) < 1e-13
+    assert rel(orc.fft(x, n, +1), np.fft.ifftn(x) * x.size) < 1e-13
+
+
+def test_fft_round_trip_and_axis_order(orc):
+    # a field varying along x only must transform into the ky=kz=0 plane
+    n = (16, 8, 4)
+    sp = gi.Spec(n=n, lo=(0, 0, 0), length=(1, 1, 1))
+    x = gi.axes(sp)[0]
+    f = np.broadcast_to(np.exp(2j * math.pi * 3 * x), (4, 8, 16)).copy()
+    F = orc.fft(f, n, -1).reshape(4, 8, 16)
+    assert abs(F[0, 0, 3] - 16 * 8 * 4) < 1e-10
+    F[0, 0, 3] = 0
+    assert np.max(np.abs(F)) < 1e-10
+    back = orc.fft(orc.fft(f, n, -1), n, +1) / f.size
+    assert rel(back, f) < 1e-14
+
+
+def test_fft_rejects_non_power_of_two(orc):
+    with pytest.raises(RuntimeError):
+        orc.fft(np.zeros(12, complex), (12,), -1)
+
+
+# ------------------------------------------------------- real-time dynamics
+@pytest.mark.parametrize("n,modes", [((64,), (3,)), ((32, 16), (2, -1)), ((8, 16, 8), (1, 2, -3))])
+def test_plane_wave_is_propagated_exactly(orc, n, modes):
+    """V=0: psi = A e^{ik.x} solves the GPE with psi(t) = A e^{i(k.x - (k^2/2 + g A^2) t)},
+    and every TSSP substep is exact for it."""
+    d = len(n)
+    L = [2 * math.pi * 2, 2 * math.pi, 2 * math.pi * 3][:d]
+    A, g, dt, steps = 0.7, 2.5, 1e-3, 50
+    sp = gi.Spec(n=n, lo=(-1.0,) * d, length=tuple(L), g=g, dt=dt, gamma=(0.0,) * d)
+    P = orc.Problem(**sp.kwargs())
+    psi0 = gi.plane_wave(sp, modes, A)
+    k2 = sum((2 * math.pi * modes[a] / L[a]) ** 2 for a in range(d))
+    t = steps * dt
+    exact = psi0 * np.exp(-1j * (k2 / 2 + g * A * A) * t)
+    assert rel(P.step_real(psi0, steps), exact) < 1e-12
+
+
+def test_norm_conserved_in_real_time(orc):
+    sp = gi.CONFIG_1D
+    P = orc.Problem(**sp.kwargs())
+    psi0 = gi.gaussian_1d(sp, seed=0)
+    n0 = P.norm_energy(psi0)[0]
+    psi = P.step_real(psi0, 1000)
+    assert abs(P.norm_energy(psi)[0] - n0) < 1e-13
+
+
+@pytest.mark.parametrize("spec", [
+    gi.CONFIG_1D,
+    gi.Spec(n=(32, 64), lo=(-6, -8), length=(12, 16), g=50.0, dt=1e-3, gamma=(1.0, 2.0)),
+    gi.Spec(n=(16, 8, 32), lo=(-5, -4, -6), length=(10, 8, 12), g=20.0, dt=2e-3,
+            gamma=(1.0, 1.5, 3.0)),
+])
+def test_time_reversal(orc, spec):
+    """Each substep is inverted by the same substep with -dt (the nonlinear
+    phase does not change |psi|), so S(-dt) S(dt) = identity."""
+    P = orc.Problem(**spec.kwargs())
+    Pm = P.replace(dt=-spec.dt)
+    psi0 = gi.random_field(spec, seed=3, smooth=0.5)
+    psi = Pm.step_real(P.step_real(psi0, 20), 20)
+    assert rel(psi, psi0) < 1e-12
+
+
+def test_bright_soliton(orc):
+    """g<0, V=0: psi = b/sqrt(-g) sech(bx) e^{i b^2 t/2} is an exact solution."""
+    g, b = -2.0, 1.5
+    A = b / math.sqrt(-g)
+    sp = gi.Spec(n=(512,), lo=(-20.0,), length=(40.0,), g=g, dt=1e-3, gamma=(0.0,))
+    x = gi.axes(sp)[0]
+    psi0 = (A / np.cosh(b * x)).astype(complex)
+    out = orc.Problem(**sp.kwargs()).step_real(psi0, 1000)
+    assert rel(out, psi0 * np.exp(1j * b * b * 1.0 / 2)) < 5e-6
+
+
+def test_bogoliubov_frequency(orc):
+    """Small density wave on a uniform condensate oscillates at
+    omega = sqrt(k^2/2 (k^2/2 + 2 g rho0)) (linearised GPE)."""
+    g, rho0, m, delta = 1.0, 1.0, 3, 1e-5
+    L = 2 * math.pi * 4
+    sp = gi.Spec(n=(64,), lo=(0.0,), length=(L,), g=g, dt=1e-3, gamma=(0.0,))
+    x = gi.axes(sp)[0]
+    k = 2 * math.pi * m / L
+    w = math.sqrt(k * k / 2 * (k * k / 2 + 2 * g * rho0))
+    psi = math.sqrt(rho0) * (1 + delta * np.cos(k * x)) + 0j
+    P = orc.Problem(**sp.kwargs())
+    t, amps = 0.0, []
+    for _ in range(8):
+        psi = P.step_real(psi, 400)
+        t += 0.4
+        rho_hat = np.fft.fft(np.abs(psi) ** 2) / sp.n[0]
+        amps.append((t, 2 * rho_hat[m].real))
+    for t, a in amps:
+        assert abs(a - 2 * delta * math.cos(w * t)) < 2e-3 * 2 * delta
+
+
+@pytest.mark.parametrize("dt,tol", [(2e-3, 3e-5), (1e-3, 8e-6)])
+def test_breathing_gaussian_rms_g0(orc, dt, tol):
+    """Dynamics validation setup of the paper at g=0: each axis is a harmonic
+    oscillator, so sigma_a^2(t) = eps/(2 gamma_a) cos^2(gamma_a t)
+    + 1/(2 gamma_a eps) sin^2(gamma_a t) (Heisenberg evolution of a real
+    Gaussian); TSSP error is O(dt^2)."""
+    eps = 0.25
+    sp = gi.Spec(n=(64, 64, 64), lo=(-8, -6, -4.5), length=(16, 12, 9), g=0.0, dt=dt,
+                 gamma=(1, 2, 4))
+    P = orc.Problem(**sp.kwargs())
+    psi = gi.bao_gaussian(sp)
+    T = 0.4
+    psi = P.step_real(psi, int(round(T / dt)))
+    r = P.rms(psi)
+    for a, ga in enumerate((1.0, 2.0, 4.0)):
+        ex = math.sqrt(eps / (2 * ga) * math.cos(ga * T) ** 2
+                       + 1 / (2 * ga * eps) * math.sin(ga * T) ** 2)
+        assert abs(r[a] - ex) / ex < tol
+    assert abs(r[3] - math.sqrt(sum(v * v for v in r[:3]))) < 1e-14
+
+
+# ---------------------------------------------------------- imaginary time
+@pytest.mark.parametrize("spec", [
+    gi.Spec(n=(128,), lo=(-10,), length=(20,), g=0.0, dt=1e-3, gamma=(1.0,)),
+    gi.Spec(n=(64, 64), lo=(-8, -6), length=(16, 12), g=0.0, dt=1e-3, gamma=(1.0, 2.0)),
+    gi.Spec(n=(32, 32, 32), lo=(-6, -4, -3), length=(12, 8, 6), g=0.0, dt=1e-3,
+            gamma=(1.0, 2.0, 4.0)),
+])
+def test_ground_state_g0_is_the_oscillator_gaussian(orc, spec):
+    """g=0 ground state: E = mu = sum gamma_a/2, sigma_a^2 = 1/(2 gamma_a)."""
+    P = orc.Problem(**spec.kwargs())
+    wide = gi.Spec(n=spec.n, lo=spec.lo, length=spec.length,
+                   gamma=tuple(0.6 * g_ for g_ in spec.gamma))
+    psi0 = gi.harmonic_gaussian(wide)
+    psi, steps, E = P.ground(psi0, max_steps=20000, etol=1e-13, check_every=50)
+    o = P.norm_energy(psi)
+    r = P.rms(psi)
+    E0 = sum(spec.gamma) / 2
+    assert abs(o[0] - 1.0) < 1e-12
+    assert abs(o[4] - E0) / E0 < 1e-6
+    assert abs(o[5] - E0) / E0 < 1e-6
+    for a in range(spec.ndim):
+        s = math.sqrt(1 / (2 * spec.gamma[a]))
+        assert abs(r[a] - s) / s < 2e-6
+
+
+def test_table1_2d_ground_states(orc):
+    """2D rows of the paper's Table 1 (r_rms and mu of the ground state in
+    V=(x^2+y^2)/2 from psi0 = pi^-1/2 e^{-r^2/2}).  128^2 on [-10,10)^2 at
+    dt=1e-3 reproduces every printed row to better than 1e-5 relative."""
+    rows = json.load(open(os.path.join(GOLDEN, "table1_2d.json")))["rows"]
+    for g, r_ref, mu_ref in rows:
+        sp = gi.Spec(n=(128, 128), lo=(-10, -10), length=(20, 20), g=g, dt=1e-3,
+                     gamma=(1.0, 1.0))
+        P = orc.Problem(**sp.kwargs())
+        psi, steps, E = P.ground(gi.harmonic_gaussian(sp), max_steps=40000, etol=1e-12,
+                                 check_every=50)
+        r = P.rms(psi)[3]
+        mu = P.norm_energy(psi)[5]
+        assert abs(r - r_ref) / r_ref < 2e-5, (g, r, r_ref)
+        assert abs(mu - mu_ref) / mu_ref < 2e-5, (g, mu, mu_ref)
+
+
+def test_imag_step_renormalises(orc):
+    sp = gi.Spec(n=(32, 32), lo=(-6, -6), length=(12, 12), g=30.0, dt=1e-3, gamma=(1, 1))
+    P = orc.Problem(**sp.kwargs())
+    psi = P.step_imag(gi.random_field(sp, seed=1, smooth=0.3) * 3.0, 5, target_norm=2.5)
+    assert abs(P.norm_energy(psi)[0] - 2.5) < 1e-12
+
+
+# -------------------------------------------------------------- diagnostics
+def test_energy_of_plane_wave(orc):
+    n = (32, 16)
+    L = (2 * math.pi * 2, 2 * math.pi)
+    A, g = 0.8, 3.0
+    sp = gi.Spec(n=n, lo=(0, 0), length=L, g=g, gamma=(0.0, 0.0))
+    psi = gi.plane_wave(sp, (3, -2), A)
+    o = orc.Problem(**sp.kwargs()).norm_energy(psi)
+    vol = L[0] * L[1]
+    k2 = (2 * math.pi * 3 / L[0]) ** 2 + (2 * math.pi * 2 / L[1]) ** 2
+    assert abs(o[0] - A * A * vol) < 1e-12 * vol
+    assert abs(o[1] - 0.5 * k2 * A * A * vol) < 1e-11 * vol
+    assert abs(o[2]) < 1e-15
+    assert abs(o[3] - 0.5 * g * A ** 4 * vol) < 1e-12 * vol
+    assert abs(o[5] - (0.5 * k2 + g * A * A)) < 1e-12
+
+
+def test_energy_of_oscillator_gaussian(orc):
+    sp = gi.Spec(n=(64, 32, 32), lo=(-8, -5, -4), length=(16, 10, 8), g=0.0,
+                 gamma=(1.0, 2.0, 3.0))
+    psi = gi.harmonic_gaussian(sp)
+    o = orc.Problem(**sp.kwargs()).norm_energy(psi)
+    assert abs(o[0] - 1) < 1e-12
+    # kinetic and potential each carry half of gamma/2 per axis
+    assert abs(o[1] - 1.5) < 1e-10 and abs(o[2] - 1.5) < 1e-10
+    assert abs(o[4] - 3.0) < 1e-10
+
+
+# ------------------------------------------------------------------ spectra
+def _velocity(psi, sp):
+    """u_a = Im(conj psi d_a psi)/|psi| with numpy spectral derivatives."""
+    ks = [2 * math.pi * np.fft.fftfreq(sp.n[a], d=sp.length[a] / sp.n[a]) for a in range(sp.ndim)]
+    for a in range(sp.ndim):
+        if sp.n[a] % 2 == 0:
+            ks[a][sp.n[a] // 2] = 0.0
+    K = list(reversed(np.meshgrid(*reversed(ks), indexing="ij")))
+    ph = np.fft.fftn(psi)
+    rho = np.abs(psi) ** 2
+    us = []
+    for a in range(sp.ndim):
+        d = np.fft.ifftn(1j * K[a] * ph)
+        us.append(np.where(rho >= 1e-30, np.imag(np.conj(psi) * d) / np.sqrt(np.maximum(rho, 1e-300)), 0.0))
+    return us
+
+
+@pytest.mark.parametrize("sp", [
+    gi.Spec(n=(64, 64), lo=(0, 0), length=(2 * math.pi * 4,) * 2, g=1.0),
+    gi.Spec(n=(32, 16, 16), lo=(0, 0, 0), length=(2 * math.pi * 2, 2 * math.pi, 2 * math.pi),
+            g=1.0),
+])
+def test_spectrum_parseval(orc, sp):
+    psi, _, _ = gi.vortex_field_2d(sp, nv=8, seed=2) if sp.ndim == 2 else (
+        gi.random_field(sp, seed=4, smooth=0.05), None, None)
+    ei, ec = orc.Problem(**sp.kwargs()).spectrum(psi)
+    us = _velocity(psi, sp)
+    half_u2 = 0.5 * sum(np.sum(u * u) for u in us) * sp.cell_volume()
+    assert abs((ei.sum() + ec.sum()) - half_u2) < 1e-12 * half_u2
+
+
+def test_spectrum_irrotational_has_no_incompressible_part(orc):
+    sp = gi.Spec(n=(64, 32), lo=(0, 0), length=(2 * math.pi, 2 * math.pi), g=1.0)
+    x, y = gi.axes(sp)
+    th = 0.3 * np.sin(2 * x)[None, :] + 0.2 * np.cos(3 * y)[:, None]
+    ei, ec = orc.Problem(**sp.kwargs()).spectrum(np.exp(1j * th))
+    assert ec.sum() > 1e-2
+    assert ei.sum() < 1e-13 * ec.sum()
+
+
+def test_spectrum_solenoidal_has_no_compressible_part(orc):
+    sp = gi.Spec(n=(32, 64), lo=(0, 0), length=(2 * math.pi, 2 * math.pi), g=1.0)
+    x, y = gi.axes(sp)
+    rho = 1.0 + 0.5 * np.cos(y)[:, None] + 0 * x[None, :]
+    psi = np.sqrt(rho) * np.exp(1j * 2 * x)[None, :]
+    ei, ec = orc.Problem(**sp.kwargs()).spectrum(psi)
+    assert ei.sum() > 1e-2
+    assert ec.sum() < 1e-13 * ei.sum()
+
+
+def test_spectrum_shell_count(orc):
+    sp = gi.Spec(n=(1024, 1024), lo=(0, 0), length=(2 * math.pi * 32,) * 2, g=1.0)
+    assert orc.Problem(**sp.kwargs()).nshells() == 725      # round(sqrt(2)*512) + 1
+
+
+# ------------------------------------------------------- input generators
+def test_vortex_field_is_periodic_and_winds_once_per_vortex():
+    sp = gi.Spec(n=(128, 128), lo=(0, 0), length=(2 * math.pi * 8,) * 2, g=1.0)
+    psi, pos, q = gi.vortex_field_2d(sp, nv=16, seed=1)
+    th = np.angle(psi)
+    h = sp.length[0] / sp.n[0]
+    # edge continuity: the wrapped phase jump across each periodic edge is no
+    # larger than the largest jump between interior neighbours
+    wrap = lambda d: (d + math.pi) % (2 * math.pi) - math.pi
+    inner = max(np.max(np.abs(wrap(np.diff(th, axis=0)))), np.max(np.abs(wrap(np.diff(th, axis=1)))))
+    assert np.max(np.abs(wrap(th[:, 0] - th[:, -1]))) <= inner + 1e-9
+    assert np.max(np.abs(wrap(th[0, :] - th[-1, :]))) <= inner + 1e-9
+    # winding number around each vortex on a small square loop
+    x, y = gi.axes(sp)
+    for (px, py), qj in zip(pos, q):
+        r = 1.2
+        pts = [(px + r * math.cos(t), py + r * math.sin(t)) for t in np.linspace(0, 2 * math.pi, 65)]
+        ang = []
+        for xx, yy in pts:
+            i = int(round((xx % sp.length[0]) / h)) % sp.n[0]
+            j = int(round((yy % sp.length[1]) / h)) % sp.n[1]
+            ang.append(th[j, i])
+        wind = sum(wrap(ang[i + 1] - ang[i]) for i in range(len(ang) - 1)) / (2 * math.pi)
+        assert round(wind) == qj
