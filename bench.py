@@ -1,0 +1,346 @@
+"""Benchmark: TSSP grid-point updates/s of the GB300 library on the 3D
+Taylor-Green workload (512^3 periodic grid, V=0, g=1, dt=1e-3, complex64 bulk
+with FP64 tables and reductions), against the HBM roofline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload tg512|turb1024|line256]
+
+One step = one real-time TSSP step over the whole grid.  The state (1 GiB)
+is larger than L2, so no flush is needed between steps.  Rank 0 prints one
+JSON line.  Under torchrun each rank advances its own replica (the single-grid
+path does not shard: replicas only, weak scaling); the time is the maximum
+over ranks.  ``--impl reference`` times the FP64 CPU oracle on the host cores
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gpe_inputs as gi  # noqa: E402
+
+WORKLOADS = {
+    "tg512": dict(spec=gi.CONFIG_3D_TG, prec="c64",
+                  name="3D Taylor-Green 512^3, complex64 bulk / FP64 tables and reductions, real time, "
+                       "dt=1e-3, V=0, g=1, box side 2*pi*16"),
+    "turb1024": dict(spec=gi.CONFIG_2D, prec="c64",
+                     name="2D quantum turbulence 1024^2, complex64, real time, dt=5e-4, V=0, g=1, "
+                          "512 vortices, box side 2*pi*32"),
+    "line256": dict(spec=gi.CONFIG_1D, prec="c128",
+                    name="1D 256 points complex128, real time, dt=1e-3, V=x^2/2, g=10"),
+}
+METRIC = "TSSP grid-point updates/s vs HBM roofline"
+UNIT = "grid-point updates/s"
+KERNEL_SOURCES = ["fft_tile.cuh", "pass_kernels.cuh", "pass_f32.cu", "pass_f64.cu"]
+
+
+def initial_state(key, spec, seed=0):
+    if key == "tg512":
+        return gi.taylor_green_3d(spec, seed=seed)
+    if key == "turb1024":
+        return gi.vortex_field_2d(spec, nv=512, seed=seed)[0]
+    return gi.gaussian_1d(spec, seed=seed)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2301_08275_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(kind, key):
+    """DRAM bytes per launch of `kind` from profiles/traffic_<key>.txt, if the
+    kernel sources are unchanged since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic_%s.txt" % key)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha") != kernel_source_hash():
+        return None
+    v = vals.get("bytes_per_launch[%s]" % kind)
+    return float(v) if v else None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = open("/tmp/gpe_bench_clocks_%d.csv" % os.getpid(), "w+")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.out is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.out.flush()
+        self.out.seek(0)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_sample(key, spec, max_seconds=25.0, steps=None):
+    """Time the FP64 oracle on the host cores: whole-grid steps of the workload
+    until about max_seconds of work (at least one step)."""
+    import oracle
+    oracle.build()
+    cores = oracle.set_threads(0)
+    psi = initial_state(key, spec).astype(np.complex128)
+    P = oracle.Problem(**spec.kwargs())
+    done, t0 = 0, time.perf_counter()
+    while True:
+        psi = P.step_real(psi, 1)
+        done += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and done >= steps) or (steps is None and (el > max_seconds or el * (done + 1) / done > max_seconds * 1.2)):
+            break
+    return dict(value=spec.N * done / el, unit=UNIT, cores=cores, kind="oracle",
+                sample="%d full-grid real-time step(s) of the same workload (%s) on the FP64 oracle, %.1f s"
+                % (done, "x".join(map(str, spec.n)), el))
+
+
+def run_reference(args, key, wl):
+    """FP64 oracle as it stands on the host cores; each step a bounded sample:
+    one oracle step on the largest cube of the same box that keeps the run
+    within a few minutes."""
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    cores = oracle.set_threads(0)
+    spec = wl["spec"]
+    budget = 150.0
+    total = args.steps + args.warmup
+    # per-point cost from a quick probe on a small cube
+    probe_n = 32 if spec.ndim == 3 else (256 if spec.ndim == 2 else spec.n[0])
+    pn = tuple([probe_n] * spec.ndim) if spec.ndim > 1 else spec.n
+    psp = gi.Spec(n=pn, lo=spec.lo, length=spec.length, g=spec.g, dt=spec.dt, gamma=spec.gamma)
+    psi = gi.random_field(psp, seed=0)
+    P = oracle.Problem(**psp.kwargs())
+    t0 = time.perf_counter()
+    P.step_real(psi, 2)
+    per_pt = (time.perf_counter() - t0) / 2 / psp.N
+    n = spec.n[0]
+    while n > 8 and per_pt * (n ** spec.ndim) * 1.3 * total > budget:
+        n //= 2
+    sn = tuple([n] * spec.ndim) if spec.ndim > 1 else spec.n
+    ssp = gi.Spec(n=sn, lo=spec.lo, length=spec.length, g=spec.g, dt=spec.dt, gamma=spec.gamma)
+    psi = initial_state(key, ssp).astype(np.complex128) if key != "line256" else initial_state(key, ssp)
+    P = oracle.Problem(**ssp.kwargs())
+    psi = P.step_real(psi, args.warmup)
+    t0 = time.perf_counter()
+    psi = P.step_real(psi, args.steps)
+    el = time.perf_counter() - t0
+    value = ssp.N * args.steps / el
+    sample = ("each step: one FP64 oracle TSSP step on a %s grid of the same box and parameters "
+              "(the full %s grid would not fit the run in minutes)" % ("x".join(map(str, sn)),
+                                                                       "x".join(map(str, spec.n))))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl["name"], "grid": list(spec.n)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, key, wl):
+    import torch
+    import paper_2301_08275_gb300 as gpe
+
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gpe.build()
+    spec = wl["spec"]
+    prec = gpe.GPE_C64 if wl["prec"] == "c64" else gpe.GPE_C128
+    cdt = torch.complex64 if prec == gpe.GPE_C64 else torch.complex128
+    stream = torch.cuda.Stream(device=dev)
+    plan = gpe.Plan(spec.n, spec.lo, spec.length, g=spec.g, dt=spec.dt, gamma=spec.gamma[: spec.ndim],
+                    prec=prec, stream=stream)
+    psi0 = initial_state(key, spec, seed=rank)
+    psi = torch.from_numpy(np.ascontiguousarray(psi0).astype(np.complex64 if prec == gpe.GPE_C64 else np.complex128)).to(dev)
+    del psi0
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    barrier()                      # the upload ran on the default stream
+    plan.step_real(psi, args.warmup)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        plan.step_real(psi, args.steps)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * spec.N * args.steps / (ms / 1e3)
+
+    # per-kernel timing over a second timed region of the same length, traced
+    plan.trace(True)
+    barrier()
+    plan.step_real(psi, args.steps)
+    barrier()
+    tr = plan.trace_read()
+    plan.trace(False)
+    launches = int(sum(c for c, _ in tr.values()))
+    dom = max(tr.items(), key=lambda kv: kv[1][1])
+    kind, (cnt, tot) = dom
+    avg_ms = tot / cnt
+    bytes_per_launch = 2.0 * spec.N * (8 if prec == gpe.GPE_C64 else 16)
+    peak, peak_src = measured_peaks()
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    traffic = read_traffic(kind, key)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": kind, "kernel_avg_ms": avg_ms,
+                "bytes_per_launch": bytes_per_launch, "peak_source": peak_src,
+                "kernels": {k: {"launches": c, "avg_ms": t / c, "share": t / sum(x[1] for x in tr.values())}
+                            for k, (c, t) in tr.items()}}
+
+    # end to end through the host-buffer entry point: every step copies the
+    # state in from pinned host memory and the result back
+    e2e_steps = max(3, min(args.steps, 20))
+    host = torch.empty(psi.shape, dtype=cdt, pin_memory=True)
+    host.copy_(psi.cpu())
+    hnp = host.numpy()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.step_real_host(hnp, 1)
+    el = time.perf_counter() - t0
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([el], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    state_bytes = spec.N * (8 if prec == gpe.GPE_C64 else 16)
+    e2e = {"value": ws * spec.N * e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+           "d2h_bytes_per_step": state_bytes, "steps": e2e_steps,
+           "api": "gpe_step_real_host (1 step per call, pinned host buffer)"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_sample(key, spec)
+
+    nrm = plan.norm_energy(psi)[0]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == gpe.GPE_C64 else "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "grid": list(spec.n),
+                       "precision": "complex64 bulk, FP64 tables and reductions" if prec == gpe.GPE_C64
+                       else "complex128",
+                       "l2": "state %.2f GiB > L2: no flush between steps" % (state_bytes / 2 ** 30)
+                       if state_bytes > 130e6 else "state fits in L2 (not flushed)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "norm_after": float(nrm[0])},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "gpu_launches": launches}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tg512", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, args.workload, wl)
+    return run_ours(args, args.workload, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,152 @@
+/*
+ * gpe.h - C ABI of the GB300 time-splitting spectral (TSSP) Gross-Pitaevskii library.
+ *
+ * The library advances solutions of the non-dimensional Gross-Pitaevskii
+ * equation (quTARANG paper, Eq. ndGPE)
+ *
+ *     i dpsi/dt = -1/2 lap psi + V psi + g |psi|^2 psi,   V = 1/2 sum_a gamma_a^2 x_a^2,
+ *
+ * on periodic grids in 1, 2 or 3 dimensions with the TSSP scheme the paper
+ * uses ("Numerical Scheme and functionalities": TSSP for dynamics, the same
+ * scheme in imaginary time t -> -i t with renormalisation after every step for
+ * ground states), and evaluates the norm, energy, chemical potential, rms sizes
+ * (Results, item 1) and the compressible / incompressible kinetic-energy
+ * spectra (feature list, item 3).
+ *
+ * Conventions shared by every entry point
+ *   Grid      n[a] points on axis a (powers of two, 2..4096; unused axes 1),
+ *             periodic box [lo[a], lo[a] + len[a]), x_j = lo + j*len/n.
+ *   Layout    psi is interleaved complex (re, im), C order with x fastest:
+ *             element (x, y, z) of instance b sits at b*N + x + n0*(y + n1*z),
+ *             N = n0*n1*n2.  complex64 (GPE_C64, 8 bytes per point) or
+ *             complex128 (GPE_C128, 16 bytes).  Device pointers are CUDA
+ *             device memory owned by the caller, 16-byte aligned.
+ *   Streams   every call is enqueued on the stream given to gpe_plan_create
+ *             (NULL: the legacy default stream).  Calls that return values to
+ *             host memory synchronise that stream before returning.
+ *   Errors    every call returns a gpe_status and never aborts the process;
+ *             gpe_last_error() gives a message for the calling thread.
+ *   Ownership a plan owns its tables, workspace and partial-sum buffers; the
+ *             caller owns psi.  Plans are not thread safe: use one per thread.
+ */
+#ifndef GPE_H
+#define GPE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gpe_status {
+    GPE_OK = 0,
+    GPE_EINVAL = 1,        /* bad argument (NULL pointer, bad size, bad flag)   */
+    GPE_EUNSUPPORTED = 2,  /* grid not supported (non power of two, >4096, ndim) */
+    GPE_ENOMEM = 3,        /* device or host allocation failed                  */
+    GPE_ECUDA = 4,         /* a CUDA runtime call failed                        */
+    GPE_ENUMERIC = 5,      /* non-finite or zero norm met                       */
+    GPE_ETIMEOUT = 6,      /* a wait ran past its limit                         */
+    GPE_EBUSY = 7,         /* admission refused: budget or slots exhausted      */
+    GPE_ENOTREADY = 8      /* polled request not finished yet                   */
+} gpe_status;
+
+typedef enum gpe_precision {
+    GPE_C64 = 0,   /* complex64 bulk arithmetic, FP64 reductions and tables */
+    GPE_C128 = 1   /* complex128 throughout                                 */
+} gpe_precision;
+
+/* Problem description (copied by gpe_plan_create). */
+typedef struct gpe_plan_desc {
+    int ndim;                   /* 1, 2 or 3                                        */
+    int64_t n[3];               /* points per axis, x first; unused axes ignored    */
+    double lo[3];               /* box corner                                        */
+    double len[3];              /* box length (> 0)                                  */
+    double g;                   /* interaction parameter                             */
+    double dt;                  /* time step (negative allowed: backward in time)    */
+    double gamma[3];            /* trap frequencies, V = 1/2 sum gamma_a^2 x_a^2      */
+    int prec;                   /* gpe_precision                                     */
+    int batch;                  /* instances stored back to back (>= 1)              */
+    const double *g_each;       /* host, batch entries overriding g, or NULL         */
+    const double *gamma_each;   /* host, batch*3 entries overriding gamma, or NULL   */
+} gpe_plan_desc;
+
+typedef struct gpe_plan gpe_plan;
+
+/* Validate desc, build the per-axis twiddle, kinetic-phase and trap-phase
+ * tables (evaluated in FP64 on the host) and allocate workspace.
+ * cuda_stream: a cudaStream_t or NULL.  On success *out owns everything. */
+gpe_status gpe_plan_create(const gpe_plan_desc *desc, void *cuda_stream, gpe_plan **out);
+gpe_status gpe_plan_destroy(gpe_plan *plan);
+
+/* Advance every instance by nsteps real-time TSSP steps in place (Numerical
+ * Scheme: TSSP of Bao et al.): per step
+ *   psi <- psi exp(-i (V + g|psi|^2) dt/2); psi_hat = FFT psi;
+ *   psi_hat <- psi_hat exp(-i |k|^2 dt/2); psi = IFFT(psi_hat)/N;
+ *   psi <- psi exp(-i (V + g|psi|^2) dt/2).
+ * Consecutive nonlinear half-steps are merged into one full step (exact:
+ * |psi| does not change under them).  psi_dev is real-space on entry and
+ * on return.  nsteps >= 0. */
+gpe_status gpe_step_real(gpe_plan *plan, void *psi_dev, int64_t nsteps);
+
+/* Same as gpe_step_real on a HOST buffer: copies psi in (pageable or pinned),
+ * steps on the device and copies the result back.  Uses plan workspace. */
+gpe_status gpe_step_real_host(gpe_plan *plan, void *psi_host, int64_t nsteps);
+
+/* Imaginary-time TSSP (ground-state paragraph: t -> -i t, renormalise each
+ * step): per step psi <- psi exp(-(V + g|psi|^2) dt/2) (|psi| frozen at the
+ * substep start), FFT, exp(-|k|^2 dt/2), IFFT/N, the same half-step again,
+ * then psi <- psi sqrt(target_norm / norm).  Runs in chunks of check_every
+ * steps and stops after a chunk once |E - E_previous_check| < etol for every
+ * instance (etol <= 0: never stops early), or after max_steps.  The first
+ * reference energy is that of the input.  steps_done (may be NULL) receives
+ * the steps taken; E_final (may be NULL) receives batch energies. */
+gpe_status gpe_step_imag(gpe_plan *plan, void *psi_dev, int64_t max_steps, double target_norm,
+                         double etol, int check_every, int64_t *steps_done, double *E_final);
+
+/* out_host[6*b + i], i = norm, E_kin, E_pot, E_int, E, mu for instance b:
+ *   norm = sum|psi|^2 dV, E_kin = 1/2 sum_k |k|^2 |psi_hat|^2 dV/N,
+ *   E_pot = sum V|psi|^2 dV, E_int = g/2 sum|psi|^4 dV, E = sum of the three,
+ *   mu = (E_kin + E_pot + 2 E_int)/norm.  Reductions in FP64. */
+gpe_status gpe_norm_energy(gpe_plan *plan, const void *psi_dev, double *out_host);
+
+/* out_host[4*b + i] = sigma_x, sigma_y, sigma_z, r_rms for instance b:
+ * sigma_a^2 = sum x_a^2|psi|^2 / sum|psi|^2 (uncentred), r_rms^2 = sum sigma_a^2
+ * (Results, item 1: r_rms = (int r^2 |psi|^2 dV)^(1/2) for unit norm). */
+gpe_status gpe_rms_size(gpe_plan *plan, const void *psi_dev, double *out_host);
+
+/* Kinetic-energy spectra (feature list, item 3).  u_a = Im(conj(psi) d_a psi)/|psi|
+ * with spectral derivatives (Nyquist mode of i k_a zeroed, u = 0 where
+ * |psi|^2 < 1e-30); u_hat = FFT u split into u_c = k(k.u_hat)/|k|^2 and
+ * u_i = u_hat - u_c; E(n) = 1/2 sum over shell n of |u|^2 dV/N with
+ * n = round(|k| / dk), dk = 2 pi / max_a len_a.
+ * kinds: GPE_SPEC_INC | GPE_SPEC_COMP.  out_host receives, for each requested
+ * kind in that order, nshells doubles per instance ([kind][b][shell]).
+ * nshells must be >= gpe_spectrum_nshells(plan). */
+#define GPE_SPEC_INC 1u
+#define GPE_SPEC_COMP 2u
+int64_t gpe_spectrum_nshells(const gpe_plan *plan);
+gpe_status gpe_spectrum(gpe_plan *plan, const void *psi_dev, unsigned kinds, double *out_host,
+                        int64_t nshells);
+
+/* Tracing (profiling aid, no counterpart in the paper).  While enabled, every
+ * kernel launch the plan makes is bracketed by two CUDA events on the plan
+ * stream and filed under a kind such as "x512:I-NR-F" (axis, line length, and
+ * the pass's substeps: F/I forward/inverse FFT, NR/NI nonlinear real/imaginary,
+ * KR/KI kinetic real/imaginary, S scale, diag/red reductions).  Enabling clears
+ * earlier records.  gpe_trace_read synchronises the stream and returns, for
+ * kind i < gpe_trace_count(), its name (NUL-terminated, truncated to name_len),
+ * the number of launches and their summed device time in milliseconds. */
+gpe_status gpe_trace_enable(gpe_plan *plan, int enable);
+int gpe_trace_count(gpe_plan *plan);
+gpe_status gpe_trace_read(gpe_plan *plan, int i, char *name, size_t name_len, int64_t *launches,
+                          double *total_ms);
+
+/* Thread-local message describing the last error (never NULL). */
+const char *gpe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPE_H */

@@ -1,0 +1,885 @@
+// api.cu - plan objects and the C ABI entry points declared in include/gpe.h.
+//
+// A plan holds, per axis, the twiddle table exp(-2 pi i t/n), the kinetic
+// substep tables exp(-i k^2 dt/2) (real time) and exp(-k^2 dt/2)/n
+// (imaginary time), and per instance the trap tables exp(-i V_a dt/2),
+// exp(-i V_a dt) and exp(-V_a dt/2) with V_a = gamma_a^2 x^2 / 2.  All are
+// evaluated in double precision on the host; in single precision the unit
+// factors are stored as hi + lo float pairs (see fft_tile.cuh).  Because the
+// trap is separable, V enters every nonlinear substep as a product of per-axis
+// unit phases and only the g|psi|^2 part of the angle is evaluated per point.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/gpe.h"
+#include "gpe_internal.h"
+
+namespace gpe {
+cudaError_t launch_pass_f32(bool rows, const PassArgs &a, cudaStream_t st);
+cudaError_t launch_pass_f64(bool rows, const PassArgs &a, cudaStream_t st);
+cudaError_t launch_line1d_f32(const Line1DArgs &a, cudaStream_t st);
+cudaError_t launch_line1d_f64(const Line1DArgs &a, cudaStream_t st);
+int lines_per_tile_f32(bool rows, int n);
+int lines_per_tile_f64(bool rows, int n);
+
+cudaError_t launch_pass(int prec, bool rows, const PassArgs &a, cudaStream_t st)
+{
+    return prec == GPE_C64 ? launch_pass_f32(rows, a, st) : launch_pass_f64(rows, a, st);
+}
+int pass_lines_per_tile(int prec, bool rows, int n)
+{
+    return prec == GPE_C64 ? lines_per_tile_f32(rows, n) : lines_per_tile_f64(rows, n);
+}
+cudaError_t launch_line1d(int prec, const Line1DArgs &a, cudaStream_t st)
+{
+    return prec == GPE_C64 ? launch_line1d_f32(a, st) : launch_line1d_f64(a, st);
+}
+}  // namespace gpe
+
+using namespace gpe;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error = "no error";
+
+static gpe_status fail(gpe_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+#define GPE_CUDA(call)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(e_ == cudaErrorMemoryAllocation ? GPE_ENOMEM : GPE_ECUDA,                \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+    } while (0)
+
+#define GPE_TRY(expr)                         \
+    do {                                      \
+        gpe_status s_ = (expr);               \
+        if (s_ != GPE_OK) return s_;          \
+    } while (0)
+
+extern "C" const char *gpe_last_error(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------------ plan
+struct gpe_plan {
+    int ndim = 0;
+    int64_t n[3] = {1, 1, 1};
+    int64_t N = 1;
+    int64_t batch = 1;
+    int prec = GPE_C64;
+    size_t csize = 8, rsize = 4;
+    double lo[3] = {0, 0, 0}, len[3] = {1, 1, 1}, h[3] = {0, 0, 0}, kf[3] = {0, 0, 0};
+    double dt = 0, dv = 1;
+    cudaStream_t st = nullptr;
+    int device = 0;
+    bool trap[3] = {false, false, false};
+    void *tw[3] = {}, *kt[3] = {}, *ki[3] = {}, *vh[3] = {}, *vf[3] = {}, *vi[3] = {};
+    double *g_dev = nullptr, *gamma_dev = nullptr, *scale = nullptr, *partials = nullptr;
+    double *sums = nullptr, *out6 = nullptr, *out4 = nullptr;
+    int *err = nullptr;
+    int64_t lines_cap = 0;
+    double *pin = nullptr;   // pinned host staging
+    size_t pin_len = 0;
+    void *work[4] = {};
+    double *hist = nullptr, *spec_out = nullptr;
+    int hist_blocks = 0;
+    int64_t nshells = 0;
+    void *host_buf = nullptr;    // device copy for gpe_step_real_host
+    std::vector<void *> allocs;
+    // tracing
+    bool tracing = false;
+    struct Rec { std::string kind; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> event_pool;
+    std::vector<std::string> kinds;
+    std::map<std::string, std::pair<int64_t, double>> totals;
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static int ilog2_64(int64_t v)
+{
+    int r = 0;
+    while ((int64_t(1) << r) < v) ++r;
+    return r;
+}
+static bool pow2(int64_t v) { return v >= 1 && (v & (v - 1)) == 0; }
+
+static gpe_status dalloc(gpe_plan *p, void **ptr, size_t bytes)
+{
+    *ptr = nullptr;
+    if (bytes == 0) return GPE_OK;
+    GPE_CUDA(cudaMalloc(ptr, bytes));
+    p->allocs.push_back(*ptr);
+    return GPE_OK;
+}
+
+// upload a double-precision table rounded to the bulk precision
+static gpe_status upload_real(gpe_plan *p, void **dst, const std::vector<double> &v)
+{
+    GPE_TRY(dalloc(p, dst, v.size() * p->rsize));
+    if (p->prec == GPE_C64) {
+        std::vector<float> f(v.begin(), v.end());
+        GPE_CUDA(cudaMemcpy(*dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+        GPE_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    return GPE_OK;
+}
+// v holds interleaved (re, im) of unit factors.  complex128: stored as is;
+// complex64: each value w becomes (hi, lo) = (fl(w), fl(w - fl(w))) so that
+// kernels can apply it without a per-application modulus error.
+static gpe_status upload_cplx(gpe_plan *p, void **dst, const std::vector<double> &v)
+{
+    if (p->prec != GPE_C64) return upload_real(p, dst, v);
+    GPE_TRY(dalloc(p, dst, v.size() * 2 * sizeof(float)));
+    std::vector<float> f(v.size() * 2);
+    for (size_t i = 0; i + 1 < v.size(); i += 2) {
+        const float hx = (float)v[i], hy = (float)v[i + 1];
+        f[2 * i + 0] = hx;
+        f[2 * i + 1] = hy;
+        f[2 * i + 2] = (float)(v[i] - (double)hx);
+        f[2 * i + 3] = (float)(v[i + 1] - (double)hy);
+    }
+    GPE_CUDA(cudaMemcpy(*dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return GPE_OK;
+}
+
+static void destroy(gpe_plan *p)
+{
+    if (!p) return;
+    for (auto &r : p->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : p->event_pool) cudaEventDestroy(e);
+    for (void *a : p->allocs) cudaFree(a);
+    if (p->pin) cudaFreeHost(p->pin);
+    delete p;
+}
+
+extern "C" gpe_status gpe_plan_create(const gpe_plan_desc *d, void *cuda_stream, gpe_plan **out)
+{
+    if (!d || !out) return fail(GPE_EINVAL, "gpe_plan_create: NULL argument");
+    *out = nullptr;
+    if (d->ndim < 1 || d->ndim > 3) return fail(GPE_EUNSUPPORTED, "ndim must be 1, 2 or 3");
+    if (d->prec != GPE_C64 && d->prec != GPE_C128) return fail(GPE_EINVAL, "prec must be GPE_C64 or GPE_C128");
+    if (d->batch < 1) return fail(GPE_EINVAL, "batch must be >= 1");
+    if (!isfinite(d->dt) || !isfinite(d->g)) return fail(GPE_EINVAL, "dt and g must be finite");
+    for (int a = 0; a < d->ndim; ++a) {
+        if (!pow2(d->n[a]) || d->n[a] < 2 || d->n[a] > 4096)
+            return fail(GPE_EUNSUPPORTED, "each n[a] must be a power of two in [2, 4096]");
+        if (!(d->len[a] > 0.0) || !isfinite(d->len[a]) || !isfinite(d->lo[a]))
+            return fail(GPE_EINVAL, "len[a] must be positive and lo[a] finite");
+    }
+    gpe_plan *p = new gpe_plan();
+    p->ndim = d->ndim;
+    p->batch = d->batch;
+    p->prec = d->prec;
+    p->csize = d->prec == GPE_C64 ? 8 : 16;
+    p->rsize = d->prec == GPE_C64 ? 4 : 8;
+    p->dt = d->dt;
+    p->st = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        destroy(p);
+        return fail(GPE_ECUDA, "cudaGetDevice failed");
+    }
+    for (int a = 0; a < 3; ++a) {
+        p->n[a] = a < d->ndim ? d->n[a] : 1;
+        p->lo[a] = a < d->ndim ? d->lo[a] : 0.0;
+        p->len[a] = a < d->ndim ? d->len[a] : 1.0;
+        p->h[a] = a < d->ndim ? d->len[a] / (double)d->n[a] : 0.0;
+        p->kf[a] = a < d->ndim ? 2.0 * M_PI / d->len[a] : 0.0;
+        p->N *= p->n[a];
+    }
+    p->dv = 1.0;
+    for (int a = 0; a < d->ndim; ++a) p->dv *= p->h[a];
+
+    const int64_t B = p->batch;
+    std::vector<double> gs(B), gam(3 * B, 0.0);
+    for (int64_t b = 0; b < B; ++b) {
+        gs[b] = d->g_each ? d->g_each[b] : d->g;
+        for (int a = 0; a < 3; ++a) {
+            double v = 0.0;
+            if (a < d->ndim) v = d->gamma_each ? d->gamma_each[3 * b + a] : d->gamma[a];
+            if (!isfinite(v) || !isfinite(gs[b])) {
+                destroy(p);
+                return fail(GPE_EINVAL, "g and gamma must be finite");
+            }
+            gam[3 * b + a] = v;
+            if (v != 0.0) p->trap[a] = true;
+        }
+    }
+    gpe_status s = GPE_OK;
+#define PLAN_TRY(expr)            \
+    do {                          \
+        s = (expr);               \
+        if (s != GPE_OK) {        \
+            destroy(p);           \
+            return s;             \
+        }                         \
+    } while (0)
+    for (int a = 0; a < d->ndim; ++a) {
+        const int64_t na = p->n[a];
+        std::vector<double> tw(2 * na), kt(2 * na), ki(na);
+        for (int64_t t = 0; t < na; ++t) {
+            const double ang = 2.0 * M_PI * (double)t / (double)na;
+            tw[2 * t] = cos(ang);
+            tw[2 * t + 1] = -sin(ang);
+            const int64_t m = t < na / 2 ? t : t - na;
+            const double k = p->kf[a] * (double)m;
+            const double th = 0.5 * k * k * p->dt;
+            kt[2 * t] = cos(th);
+            kt[2 * t + 1] = -sin(th);
+            ki[t] = exp(-th) / (double)na;
+        }
+        PLAN_TRY(upload_cplx(p, &p->tw[a], tw));
+        PLAN_TRY(upload_cplx(p, &p->kt[a], kt));
+        PLAN_TRY(upload_real(p, &p->ki[a], ki));
+        if (p->trap[a]) {
+            std::vector<double> vh(2 * na * B), vf(2 * na * B), vi(na * B);
+            for (int64_t b = 0; b < B; ++b) {
+                const double ga = gam[3 * b + a];
+                for (int64_t j = 0; j < na; ++j) {
+                    const double x = p->lo[a] + (double)j * p->h[a];
+                    const double V = 0.5 * ga * ga * x * x;
+                    const double th = V * p->dt;
+                    vh[2 * (b * na + j)] = cos(0.5 * th);
+                    vh[2 * (b * na + j) + 1] = -sin(0.5 * th);
+                    vf[2 * (b * na + j)] = cos(th);
+                    vf[2 * (b * na + j) + 1] = -sin(th);
+                    vi[b * na + j] = exp(-0.5 * th);
+                }
+            }
+            PLAN_TRY(upload_cplx(p, &p->vh[a], vh));
+            PLAN_TRY(upload_cplx(p, &p->vf[a], vf));
+            PLAN_TRY(upload_real(p, &p->vi[a], vi));
+        }
+    }
+    // per-instance parameters and reduction buffers (always double precision)
+    int64_t maxlines = 0;
+    for (int a = 0; a < d->ndim; ++a) maxlines = std::max<int64_t>(maxlines, p->N / p->n[a]);
+    p->lines_cap = maxlines * B;
+    PLAN_TRY(dalloc(p, (void **)&p->g_dev, sizeof(double) * B));
+    PLAN_TRY(dalloc(p, (void **)&p->gamma_dev, sizeof(double) * 3 * B));
+    PLAN_TRY(dalloc(p, (void **)&p->scale, sizeof(double) * B));
+    PLAN_TRY(dalloc(p, (void **)&p->partials, sizeof(double) * NQ * p->lines_cap));
+    PLAN_TRY(dalloc(p, (void **)&p->sums, sizeof(double) * NQ * B));
+    PLAN_TRY(dalloc(p, (void **)&p->out6, sizeof(double) * 6 * B));
+    PLAN_TRY(dalloc(p, (void **)&p->out4, sizeof(double) * 4 * B));
+    PLAN_TRY(dalloc(p, (void **)&p->err, sizeof(int)));
+#undef PLAN_TRY
+    if (cudaMemcpy(p->g_dev, gs.data(), sizeof(double) * B, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->gamma_dev, gam.data(), sizeof(double) * 3 * B, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess) {
+        destroy(p);
+        return fail(GPE_ECUDA, "uploading plan parameters failed");
+    }
+    p->pin_len = (size_t)B * 6 + 64;
+    if (cudaMallocHost((void **)&p->pin, sizeof(double) * p->pin_len) != cudaSuccess) {
+        p->pin = nullptr;
+        destroy(p);
+        return fail(GPE_ENOMEM, "pinned host staging allocation failed");
+    }
+    *out = p;
+    return GPE_OK;
+}
+
+extern "C" gpe_status gpe_plan_destroy(gpe_plan *p)
+{
+    if (!p) return fail(GPE_EINVAL, "gpe_plan_destroy: NULL plan");
+    DeviceGuard dg(p->device);
+    if (p->st) cudaStreamSynchronize(p->st);
+    else cudaDeviceSynchronize();
+    destroy(p);
+    return GPE_OK;
+}
+
+// ------------------------------------------------------------------ tracing
+static cudaEvent_t pool_event(gpe_plan *p)
+{
+    if (!p->event_pool.empty()) {
+        cudaEvent_t e = p->event_pool.back();
+        p->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Bracket one launch with events when tracing is on.
+struct TraceScope {
+    gpe_plan *p;
+    std::string kind;
+    cudaEvent_t a = nullptr;
+    TraceScope(gpe_plan *p_, std::string k) : p(p_), kind(std::move(k))
+    {
+        if (p->tracing && (a = pool_event(p))) cudaEventRecord(a, p->st);
+    }
+    ~TraceScope()
+    {
+        if (!a) return;
+        cudaEvent_t b = pool_event(p);
+        if (!b) { p->event_pool.push_back(a); return; }
+        cudaEventRecord(b, p->st);
+        p->recs.push_back({kind, a, b});
+    }
+};
+
+static gpe_status trace_flush(gpe_plan *p)
+{
+    if (p->recs.empty()) return GPE_OK;
+    GPE_CUDA(cudaStreamSynchronize(p->st));
+    for (auto &r : p->recs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        auto it = p->totals.find(r.kind);
+        if (it == p->totals.end()) {
+            p->kinds.push_back(r.kind);
+            p->totals[r.kind] = {1, (double)ms};
+        } else {
+            it->second.first += 1;
+            it->second.second += ms;
+        }
+        p->event_pool.push_back(r.a);
+        p->event_pool.push_back(r.b);
+    }
+    p->recs.clear();
+    return GPE_OK;
+}
+
+extern "C" gpe_status gpe_trace_enable(gpe_plan *p, int enable)
+{
+    if (!p) return fail(GPE_EINVAL, "NULL plan");
+    DeviceGuard dg(p->device);
+    GPE_TRY(trace_flush(p));
+    p->kinds.clear();
+    p->totals.clear();
+    p->tracing = enable != 0;
+    return GPE_OK;
+}
+
+extern "C" int gpe_trace_count(gpe_plan *p)
+{
+    if (!p) return -1;
+    DeviceGuard dg(p->device);
+    if (trace_flush(p) != GPE_OK) return -1;
+    return (int)p->kinds.size();
+}
+
+extern "C" gpe_status gpe_trace_read(gpe_plan *p, int i, char *name, size_t name_len, int64_t *launches,
+                                     double *total_ms)
+{
+    if (!p) return fail(GPE_EINVAL, "NULL plan");
+    DeviceGuard dg(p->device);
+    GPE_TRY(trace_flush(p));
+    if (i < 0 || i >= (int)p->kinds.size()) return fail(GPE_EINVAL, "trace index out of range");
+    const std::string &k = p->kinds[i];
+    if (name && name_len) {
+        size_t m = std::min(name_len - 1, k.size());
+        memcpy(name, k.data(), m);
+        name[m] = 0;
+    }
+    if (launches) *launches = p->totals[k].first;
+    if (total_ms) *total_ms = p->totals[k].second;
+    return GPE_OK;
+}
+
+static const char *op_tag(int op)
+{
+    switch (op) {
+    case OP_NREAL: return "NR";
+    case OP_NIMAG: return "NI";
+    case OP_KREAL: return "KR";
+    case OP_KIMAG: return "KI";
+    case OP_SCALE_NIMAG: return "S-NI";
+    case OP_SCALE: return "S";
+    default: return "";
+    }
+}
+
+static std::string pass_kind(const PassArgs &a)
+{
+    std::string s = std::string(1, "xyz"[a.axis]) + std::to_string(a.nax) + ":";
+    if (a.red == RED_DIAG_X || a.red == RED_DIAG_K) return s + "diag";
+    std::vector<std::string> parts;
+    auto add = [&](const char *t) { if (*t) parts.push_back(t); };
+    add(op_tag(a.op_pre));
+    add(a.fft1 < 0 ? "F" : a.fft1 > 0 ? "I" : "");
+    add(op_tag(a.op_mid));
+    add(a.fft2 < 0 ? "F" : a.fft2 > 0 ? "I" : "");
+    add(op_tag(a.op_post));
+    if (a.red == RED_NORM) parts.push_back("red");
+    for (size_t i = 0; i < parts.size(); ++i) s += (i ? "-" : "") + parts[i];
+    return s;
+}
+
+// ------------------------------------------------------------------ pass setup
+// Geometry of a sweep along `axis` over `batch` instances starting at src/dst.
+static PassArgs make_pass(const gpe_plan *p, int axis, const void *src, void *dst, int64_t batch)
+{
+    PassArgs a;
+    memset(&a, 0, sizeof(a));
+    const int64_t n0 = p->n[0], n1 = p->n[1];
+    a.src = src;
+    a.dst = dst;
+    a.nax = (int)p->n[axis];
+    a.axis = axis;
+    const int64_t lpi = p->N / p->n[axis];
+    a.lg_lpi = ilog2_64(lpi);
+    a.inst_stride = p->N;
+    int o0 = -1, o1 = -1;
+    if (axis == 0) {
+        a.lg_A = 0;
+        a.Sb = n0;
+        a.estride = 1;
+        o0 = 1;
+        o1 = 2;
+    } else if (axis == 1) {
+        a.lg_A = ilog2_64(n0);
+        a.Sb = n0 * n1;
+        a.estride = n0;
+        o0 = 0;
+        o1 = 2;
+    } else {
+        a.lg_A = ilog2_64(n0 * n1);
+        a.Sb = p->N;
+        a.estride = n0 * n1;
+        o0 = 0;
+        o1 = 1;
+    }
+    a.o0n = (int)p->n[o0];
+    a.o1n = (int)p->n[o1];
+    a.lg_o0 = ilog2_64(p->n[o0]);
+    a.lines_total = batch * lpi;
+    const int L = pass_lines_per_tile(p->prec, axis == 0, a.nax);
+    a.ntiles = (a.lines_total + L - 1) / L;
+    a.tw = p->tw[axis];
+    const bool h0 = o0 < p->ndim, h1 = o1 < p->ndim;
+    a.kt_ax = p->kt[axis];
+    a.kt_o0 = h0 ? p->kt[o0] : nullptr;
+    a.kt_o1 = h1 ? p->kt[o1] : nullptr;
+    a.ki_ax = p->ki[axis];
+    a.ki_o0 = h0 ? p->ki[o0] : nullptr;
+    a.ki_o1 = h1 ? p->ki[o1] : nullptr;
+    a.vi_ax = p->vi[axis];
+    a.vi_o0 = h0 ? p->vi[o0] : nullptr;
+    a.vi_o1 = h1 ? p->vi[o1] : nullptr;
+    a.g = p->g_dev;
+    a.inv_n = 1.0 / (double)p->N;
+    a.scale = p->scale;
+    a.partials = p->partials;
+    a.lines_cap = p->lines_cap;
+    a.gamma = p->gamma_dev;
+    for (int i = 0; i < 3; ++i) {
+        a.lo[i] = i < p->ndim ? p->lo[i] : 0.0;
+        a.h[i] = i < p->ndim ? p->h[i] : 0.0;
+        a.kf[i] = p->kf[i];
+    }
+    a.fft1 = a.fft2 = 0;
+    a.op_pre = a.op_mid = a.op_post = OP_NONE;
+    a.red = RED_NONE;
+    return a;
+}
+
+// select the real-time trap tables for a nonlinear substep of length c*dt (c = 1/2 or 1)
+static void set_nreal(const gpe_plan *p, PassArgs &a, bool full)
+{
+    void *const *vt = full ? p->vf : p->vh;
+    const int axis = a.axis;
+    const int o0 = axis == 0 ? 1 : 0, o1 = axis == 2 ? 1 : 2;
+    a.vt_ax = vt[axis];
+    a.vt_o0 = o0 < p->ndim ? vt[o0] : nullptr;
+    a.vt_o1 = o1 < p->ndim ? vt[o1] : nullptr;
+    a.nl_c = full ? p->dt : 0.5 * p->dt;
+}
+
+static gpe_status run(gpe_plan *p, const PassArgs &a)
+{
+    TraceScope ts(p, pass_kind(a));
+    cudaError_t e = launch_pass(p->prec, a.axis == 0, a, p->st);
+    if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("pass launch: ") + cudaGetErrorString(e));
+    return GPE_OK;
+}
+
+static gpe_status check_psi(const gpe_plan *p, const void *psi)
+{
+    if (!p) return fail(GPE_EINVAL, "NULL plan");
+    if (!psi) return fail(GPE_EINVAL, "NULL psi");
+    if (((uintptr_t)psi) % 16 != 0) return fail(GPE_EINVAL, "psi must be 16-byte aligned");
+    return GPE_OK;
+}
+
+// ------------------------------------------------------------------ real time
+static gpe_status step_real_dev(gpe_plan *p, void *psi, int64_t nsteps)
+{
+    if (nsteps == 0) return GPE_OK;
+    const int64_t B = p->batch;
+    if (p->ndim == 1) {
+        const int64_t chunk = 1 << 16;
+        for (int64_t done = 0; done < nsteps; done += chunk) {
+            Line1DArgs l;
+            memset(&l, 0, sizeof(l));
+            l.psi = psi;
+            l.batch = B;
+            l.n = (int)p->n[0];
+            l.nsteps = std::min(chunk, nsteps - done);
+            l.imag = 0;
+            l.tw = p->tw[0];
+            l.kt = p->kt[0];
+            l.vh = p->vh[0];
+            l.vf = p->vf[0];
+            l.g = p->g_dev;
+            l.dt = p->dt;
+            l.err = p->err;
+            TraceScope ts(p, "line1d" + std::to_string(l.n) + ":real");
+            cudaError_t e = launch_line1d(p->prec, l, p->st);
+            if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("1D launch: ") + cudaGetErrorString(e));
+        }
+        return GPE_OK;
+    }
+    // prologue: first nonlinear half-step and forward transforms of all but the last axis
+    PassArgs x0 = make_pass(p, 0, psi, psi, B);
+    x0.op_pre = OP_NREAL;
+    set_nreal(p, x0, false);
+    x0.fft1 = -1;
+    GPE_TRY(run(p, x0));
+    if (p->ndim == 3) {
+        PassArgs y = make_pass(p, 1, psi, psi, B);
+        y.fft1 = -1;
+        GPE_TRY(run(p, y));
+    }
+    const int piv = p->ndim - 1;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        const bool last = s == nsteps - 1;
+        PassArgs k = make_pass(p, piv, psi, psi, B);
+        k.fft1 = -1;
+        k.op_mid = OP_KREAL;
+        k.fft2 = +1;
+        GPE_TRY(run(p, k));
+        if (p->ndim == 3) {
+            PassArgs y = make_pass(p, 1, psi, psi, B);
+            y.fft1 = +1;
+            GPE_TRY(run(p, y));
+        }
+        PassArgs x = make_pass(p, 0, psi, psi, B);
+        x.fft1 = +1;
+        x.op_mid = OP_NREAL;
+        set_nreal(p, x, !last);
+        x.fft2 = last ? 0 : -1;
+        GPE_TRY(run(p, x));
+        if (p->ndim == 3 && !last) {
+            PassArgs y = make_pass(p, 1, psi, psi, B);
+            y.fft1 = -1;
+            GPE_TRY(run(p, y));
+        }
+    }
+    return GPE_OK;
+}
+
+extern "C" gpe_status gpe_step_real(gpe_plan *p, void *psi, int64_t nsteps)
+{
+    GPE_TRY(check_psi(p, psi));
+    if (nsteps < 0) return fail(GPE_EINVAL, "nsteps must be >= 0");
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return fail(GPE_ECUDA, "cannot select the plan's device");
+    return step_real_dev(p, psi, nsteps);
+}
+
+extern "C" gpe_status gpe_step_real_host(gpe_plan *p, void *psi_host, int64_t nsteps)
+{
+    if (!p || !psi_host) return fail(GPE_EINVAL, "NULL argument");
+    if (nsteps < 0) return fail(GPE_EINVAL, "nsteps must be >= 0");
+    DeviceGuard dg(p->device);
+    const size_t bytes = (size_t)p->batch * (size_t)p->N * p->csize;
+    if (!p->host_buf) GPE_TRY(dalloc(p, &p->host_buf, bytes));
+    GPE_CUDA(cudaMemcpyAsync(p->host_buf, psi_host, bytes, cudaMemcpyHostToDevice, p->st));
+    GPE_TRY(step_real_dev(p, p->host_buf, nsteps));
+    GPE_CUDA(cudaMemcpyAsync(psi_host, p->host_buf, bytes, cudaMemcpyDeviceToHost, p->st));
+    GPE_CUDA(cudaStreamSynchronize(p->st));
+    return GPE_OK;
+}
+
+// ------------------------------------------------------------------ diagnostics
+// norm/energy/rms of psi into p->out6 / p->out4 (device), enqueued on p->st
+static gpe_status diag_dev(gpe_plan *p, const void *psi)
+{
+    const int64_t B = p->batch;
+    PassArgs x = make_pass(p, 0, psi, nullptr, B);
+    x.red = RED_DIAG_X;
+    GPE_TRY(run(p, x));
+    for (int a = 1; a < p->ndim; ++a) {
+        PassArgs k = make_pass(p, a, psi, nullptr, B);
+        k.red = RED_DIAG_K;
+        GPE_TRY(run(p, k));
+    }
+    cudaError_t e = launch_reduce_lines(p->partials, p->lines_cap, 0, 7, B, p->N / p->n[0], p->sums, p->st);
+    for (int a = 1; a < p->ndim && e == cudaSuccess; ++a)
+        e = launch_reduce_lines(p->partials, p->lines_cap, 6 + a, 1, B, p->N / p->n[a], p->sums, p->st);
+    if (e == cudaSuccess) e = launch_finish_diag(p->sums, B, p->ndim, p->n, p->dv, p->g_dev, p->out6, p->out4, p->st);
+    if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("diagnostics: ") + cudaGetErrorString(e));
+    return GPE_OK;
+}
+
+static gpe_status copy_out(gpe_plan *p, const double *dev, size_t count, double *host)
+{
+    GPE_CUDA(cudaMemcpyAsync(host, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, p->st));
+    GPE_CUDA(cudaStreamSynchronize(p->st));
+    return GPE_OK;
+}
+
+extern "C" gpe_status gpe_norm_energy(gpe_plan *p, const void *psi, double *out)
+{
+    GPE_TRY(check_psi(p, psi));
+    if (!out) return fail(GPE_EINVAL, "NULL output");
+    DeviceGuard dg(p->device);
+    GPE_TRY(diag_dev(p, psi));
+    return copy_out(p, p->out6, 6 * (size_t)p->batch, out);
+}
+
+extern "C" gpe_status gpe_rms_size(gpe_plan *p, const void *psi, double *out)
+{
+    GPE_TRY(check_psi(p, psi));
+    if (!out) return fail(GPE_EINVAL, "NULL output");
+    DeviceGuard dg(p->device);
+    GPE_TRY(diag_dev(p, psi));
+    return copy_out(p, p->out4, 4 * (size_t)p->batch, out);
+}
+
+// ------------------------------------------------------------------ imaginary time
+static gpe_status fill_scale_one(gpe_plan *p)
+{
+    for (int64_t b = 0; b < p->batch && b < (int64_t)p->pin_len; ++b) p->pin[b] = 1.0;
+    // pin_len >= batch by construction
+    GPE_CUDA(cudaMemcpyAsync(p->scale, p->pin, sizeof(double) * p->batch, cudaMemcpyHostToDevice, p->st));
+    GPE_CUDA(cudaStreamSynchronize(p->st));
+    return GPE_OK;
+}
+
+static gpe_status imag_steps(gpe_plan *p, void *psi, int64_t nsteps, double target)
+{
+    const int64_t B = p->batch;
+    if (nsteps <= 0) return GPE_OK;
+    if (p->ndim == 1) {
+        Line1DArgs l;
+        memset(&l, 0, sizeof(l));
+        l.psi = psi;
+        l.batch = B;
+        l.n = (int)p->n[0];
+        l.nsteps = nsteps;
+        l.imag = 1;
+        l.tw = p->tw[0];
+        l.kt = p->ki[0];
+        l.vi = p->vi[0];
+        l.g = p->g_dev;
+        l.dt = p->dt;
+        l.target_norm_over_dv = target / p->dv;
+        l.err = p->err;
+        TraceScope ts(p, "line1d" + std::to_string(l.n) + ":imag");
+        cudaError_t e = launch_line1d(p->prec, l, p->st);
+        if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("1D launch: ") + cudaGetErrorString(e));
+        return GPE_OK;
+    }
+    GPE_TRY(fill_scale_one(p));
+    const int piv = p->ndim - 1;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        PassArgs x = make_pass(p, 0, psi, psi, B);
+        x.op_pre = OP_SCALE_NIMAG;
+        x.nl_c = 0.5 * p->dt;
+        x.fft1 = -1;
+        GPE_TRY(run(p, x));
+        if (p->ndim == 3) {
+            PassArgs y = make_pass(p, 1, psi, psi, B);
+            y.fft1 = -1;
+            GPE_TRY(run(p, y));
+        }
+        PassArgs k = make_pass(p, piv, psi, psi, B);
+        k.fft1 = -1;
+        k.op_mid = OP_KIMAG;
+        k.fft2 = +1;
+        GPE_TRY(run(p, k));
+        if (p->ndim == 3) {
+            PassArgs y = make_pass(p, 1, psi, psi, B);
+            y.fft1 = +1;
+            GPE_TRY(run(p, y));
+        }
+        PassArgs x2 = make_pass(p, 0, psi, psi, B);
+        x2.fft1 = +1;
+        x2.op_mid = OP_NIMAG;
+        x2.nl_c = 0.5 * p->dt;
+        x2.red = RED_NORM;
+        GPE_TRY(run(p, x2));
+        cudaError_t e = launch_reduce_lines(p->partials, p->lines_cap, 0, 1, B, p->N / p->n[0], p->sums, p->st);
+        if (e == cudaSuccess) e = launch_finish_scale(p->sums, B, p->dv, target, p->scale, p->err, p->st);
+        if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("renormalisation: ") + cudaGetErrorString(e));
+    }
+    // apply the last renormalisation
+    PassArgs xs = make_pass(p, 0, psi, psi, B);
+    xs.op_pre = OP_SCALE;
+    GPE_TRY(run(p, xs));
+    return GPE_OK;
+}
+
+static gpe_status check_err(gpe_plan *p)
+{
+    int h = 0;
+    GPE_CUDA(cudaMemcpyAsync(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+    GPE_CUDA(cudaStreamSynchronize(p->st));
+    if (h) {
+        cudaMemsetAsync(p->err, 0, sizeof(int), p->st);
+        cudaStreamSynchronize(p->st);
+        return fail(GPE_ENUMERIC, "norm became zero or non-finite during imaginary time");
+    }
+    return GPE_OK;
+}
+
+extern "C" gpe_status gpe_step_imag(gpe_plan *p, void *psi, int64_t max_steps, double target_norm, double etol,
+                                    int check_every, int64_t *steps_done, double *E_final)
+{
+    GPE_TRY(check_psi(p, psi));
+    if (max_steps < 0) return fail(GPE_EINVAL, "max_steps must be >= 0");
+    if (check_every < 1) return fail(GPE_EINVAL, "check_every must be >= 1");
+    if (!(target_norm > 0.0) || !isfinite(target_norm)) return fail(GPE_EINVAL, "target_norm must be positive");
+    DeviceGuard dg(p->device);
+    const int64_t B = p->batch;
+    std::vector<double> eprev(B), ecur(B);
+    GPE_TRY(diag_dev(p, psi));
+    GPE_TRY(copy_out(p, p->out6, 6 * (size_t)B, p->pin));
+    for (int64_t b = 0; b < B; ++b) eprev[b] = p->pin[6 * b + 4];
+    int64_t done = 0;
+    while (done < max_steps) {
+        const int64_t chunk = std::min<int64_t>(check_every, max_steps - done);
+        GPE_TRY(imag_steps(p, psi, chunk, target_norm));
+        done += chunk;
+        GPE_TRY(check_err(p));
+        GPE_TRY(diag_dev(p, psi));
+        GPE_TRY(copy_out(p, p->out6, 6 * (size_t)B, p->pin));
+        bool all = etol > 0.0;
+        for (int64_t b = 0; b < B; ++b) {
+            ecur[b] = p->pin[6 * b + 4];
+            if (!isfinite(ecur[b])) return fail(GPE_ENUMERIC, "energy became non-finite");
+            if (!(fabs(ecur[b] - eprev[b]) < etol)) all = false;
+            eprev[b] = ecur[b];
+        }
+        if (all) break;
+    }
+    if (steps_done) *steps_done = done;
+    if (E_final)
+        for (int64_t b = 0; b < B; ++b) E_final[b] = eprev[b];
+    return GPE_OK;
+}
+
+// ------------------------------------------------------------------ spectra
+static int64_t nshells_of(const gpe_plan *p)
+{
+    double lmax = 0.0;
+    for (int a = 0; a < p->ndim; ++a) lmax = std::max(lmax, p->len[a]);
+    double q2 = 0.0;
+    for (int a = 0; a < p->ndim; ++a) {
+        const double q = (double)(p->n[a] / 2) * (lmax / p->len[a]);
+        q2 += q * q;
+    }
+    return (int64_t)floor(sqrt(q2) + 0.5) + 1;
+}
+
+extern "C" int64_t gpe_spectrum_nshells(const gpe_plan *p)
+{
+    if (!p) return -1;
+    return nshells_of(p);
+}
+
+// forward (dir=-1) or inverse (+1) transform of one instance over all axes, src -> dst
+static gpe_status fft_nd(gpe_plan *p, const void *src, void *dst, int dir)
+{
+    for (int a = 0; a < p->ndim; ++a) {
+        PassArgs t = make_pass(p, a, a == 0 ? src : dst, dst, 1);
+        t.fft1 = dir;
+        GPE_TRY(run(p, t));
+    }
+    return GPE_OK;
+}
+
+extern "C" gpe_status gpe_spectrum(gpe_plan *p, const void *psi, unsigned kinds, double *out, int64_t nshells)
+{
+    GPE_TRY(check_psi(p, psi));
+    if (!out) return fail(GPE_EINVAL, "NULL output");
+    if (!(kinds & (GPE_SPEC_INC | GPE_SPEC_COMP)) || (kinds & ~(GPE_SPEC_INC | GPE_SPEC_COMP)))
+        return fail(GPE_EINVAL, "kinds must be a non-empty combination of GPE_SPEC_INC and GPE_SPEC_COMP");
+    const int64_t ns = nshells_of(p);
+    if (nshells < ns) return fail(GPE_EINVAL, "nshells smaller than gpe_spectrum_nshells()");
+    if (ns > 6144) return fail(GPE_EUNSUPPORTED, "too many spectral shells");
+    DeviceGuard dg(p->device);
+    SpecArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.prec = p->prec;
+    sa.ndim = p->ndim;
+    double lmax = 0.0;
+    for (int a = 0; a < p->ndim; ++a) lmax = std::max(lmax, p->len[a]);
+    for (int a = 0; a < 3; ++a) {
+        sa.n[a] = p->n[a];
+        sa.kf[a] = p->kf[a];
+        sa.lratio[a] = a < p->ndim ? lmax / p->len[a] : 0.0;
+    }
+    sa.N = p->N;
+    const size_t field = (size_t)p->N * p->csize;
+    if (!p->work[0]) {
+        for (int w = 0; w <= p->ndim; ++w) GPE_TRY(dalloc(p, &p->work[w], field));
+    }
+    const int nb = bin_blocks(sa);
+    if (!p->hist || p->nshells < ns || p->hist_blocks < nb) {
+        GPE_TRY(dalloc(p, (void **)&p->hist, sizeof(double) * 2 * (size_t)ns * nb));
+        GPE_TRY(dalloc(p, (void **)&p->spec_out, sizeof(double) * 2 * (size_t)ns));
+        p->nshells = ns;
+        p->hist_blocks = nb;
+    }
+    std::vector<double> tmp(2 * ns);
+    const int nk = ((kinds & GPE_SPEC_INC) ? 1 : 0) + ((kinds & GPE_SPEC_COMP) ? 1 : 0);
+    for (int64_t b = 0; b < p->batch; ++b) {
+        const char *pb = (const char *)psi + (size_t)b * field;
+        GPE_TRY(fft_nd(p, pb, p->work[0], -1));
+        for (int a = 0; a < p->ndim; ++a) {
+            cudaError_t e = launch_deriv(sa, p->work[0], p->work[1 + a], a, p->st);
+            if (e != cudaSuccess) return fail(GPE_ECUDA, cudaGetErrorString(e));
+            GPE_TRY(fft_nd(p, p->work[1 + a], p->work[1 + a], +1));
+            e = launch_velocity(sa, pb, p->work[1 + a], p->st);
+            if (e != cudaSuccess) return fail(GPE_ECUDA, cudaGetErrorString(e));
+            GPE_TRY(fft_nd(p, p->work[1 + a], p->work[1 + a], -1));
+        }
+        void *uh[3] = {p->work[1], p->ndim > 1 ? p->work[2] : nullptr, p->ndim > 2 ? p->work[3] : nullptr};
+        cudaError_t e = launch_bin(sa, uh, ns, p->hist, nb, p->st);
+        if (e == cudaSuccess)
+            e = launch_hist_reduce(p->hist, nb, ns, p->dv / (double)p->N, p->spec_out, p->spec_out + ns, p->st);
+        if (e != cudaSuccess) return fail(GPE_ECUDA, cudaGetErrorString(e));
+        GPE_CUDA(cudaMemcpyAsync(tmp.data(), p->spec_out, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost, p->st));
+        GPE_CUDA(cudaStreamSynchronize(p->st));
+        int kslot = 0;
+        for (int kind = 0; kind < 2; ++kind) {
+            if (!(kinds & (kind == 0 ? GPE_SPEC_INC : GPE_SPEC_COMP))) continue;
+            double *dst = out + ((size_t)kslot * p->batch + b) * nshells;
+            for (int64_t s = 0; s < nshells; ++s) dst[s] = s < ns ? tmp[kind * ns + s] : 0.0;
+            ++kslot;
+        }
+        (void)nk;
+    }
+    return GPE_OK;
+}

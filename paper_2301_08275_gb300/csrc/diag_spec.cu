@@ -1,0 +1,259 @@
+// diag_spec.cu - FP64 reductions (norm, energy, mu, rms sizes, renormalisation
+// factor) and the kernels of the kinetic-energy spectra.
+#include <math.h>
+
+#include "fft_tile.cuh"
+#include "gpe_internal.h"
+
+namespace gpe {
+
+// ------------------------------------------------------------------ reductions
+// sums[b*NQ + q] = sum over the lines of instance b of partials[q][line], in a
+// fixed order (strided per-thread sums, then a shared-memory tree).
+__global__ void __launch_bounds__(256) k_reduce_lines(const double *__restrict__ partials, int64_t cap, int q0,
+                                                      int64_t lpi, double *__restrict__ sums)
+{
+    __shared__ double sh[256];
+    const int b = blockIdx.x, q = q0 + blockIdx.y, t = threadIdx.x;
+    const double *p = partials + (int64_t)q * cap + (int64_t)b * lpi;
+    double s = 0.0;
+    for (int64_t j = t; j < lpi; j += 256) s += p[j];
+    sh[t] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w) sh[t] += sh[t + w];
+        __syncthreads();
+    }
+    if (t == 0) sums[(int64_t)b * NQ + q] = sh[0];
+}
+
+// Renormalisation of the imaginary-time step: s_b = sqrt(target / (sum rho dV)).
+__global__ void k_finish_scale(const double *__restrict__ sums, int64_t batch, double dv, double target,
+                               double *__restrict__ scale, int *err)
+{
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const double nrm = sums[b * NQ + 0] * dv;
+    if (!(nrm > 0.0) || !isfinite(nrm)) {
+        atomicExch(err, 1);
+        scale[b] = 1.0;
+    } else {
+        scale[b] = sqrt(target / nrm);
+    }
+}
+
+// norm, E_kin, E_pot, E_int, E, mu and sigma_x, sigma_y, sigma_z, r_rms from the
+// per-instance sums of the diagnostic passes.
+__global__ void k_finish_diag(const double *__restrict__ sums, int64_t batch, int ndim, int64_t n0, int64_t n1,
+                              int64_t n2, double dv, const double *__restrict__ g, double *__restrict__ out6,
+                              double *__restrict__ out4)
+{
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const double *q = sums + b * NQ;
+    const double nrm = q[0] * dv;
+    const double n[3] = {(double)n0, (double)n1, (double)n2};
+    double ek = 0.0;
+    for (int a = 0; a < ndim; ++a) ek += q[6 + a] / n[a];
+    ek *= 0.5 * dv;
+    const double ep = q[4] * dv;
+    const double ei = 0.5 * g[b] * q[5] * dv;
+    out6[6 * b + 0] = nrm;
+    out6[6 * b + 1] = ek;
+    out6[6 * b + 2] = ep;
+    out6[6 * b + 3] = ei;
+    out6[6 * b + 4] = ek + ep + ei;
+    out6[6 * b + 5] = (ek + ep + 2.0 * ei) / nrm;
+    double r2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double s2 = a < ndim ? q[1 + a] / q[0] : 0.0;
+        out4[4 * b + a] = sqrt(s2);
+        r2 += s2;
+    }
+    out4[4 * b + 3] = sqrt(r2);
+}
+
+cudaError_t launch_reduce_lines(const double *partials, int64_t lines_cap, int nq_first, int nq, int64_t batch,
+                                int64_t lines_per_inst, double *sums, cudaStream_t st)
+{
+    dim3 grid((unsigned)batch, (unsigned)nq);
+    k_reduce_lines<<<grid, 256, 0, st>>>(partials, lines_cap, nq_first, lines_per_inst, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_scale(const double *sums, int64_t batch, double dv, double target, double *scale,
+                                int *err, cudaStream_t st)
+{
+    const int nb = (int)((batch + 127) / 128);
+    k_finish_scale<<<nb, 128, 0, st>>>(sums, batch, dv, target, scale, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_diag(const double *sums, int64_t batch, int ndim, const int64_t *n, double dv,
+                               const double *g, double *out6, double *out4, cudaStream_t st)
+{
+    const int nb = (int)((batch + 127) / 128);
+    k_finish_diag<<<nb, 128, 0, st>>>(sums, batch, ndim, n[0], n[1], n[2], dv, g, out6, out4);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ spectra
+__device__ __forceinline__ int64_t axis_index(int64_t i, const SpecArgs &s, int axis)
+{
+    int64_t stride = 1;
+    for (int a = 0; a < axis; ++a) stride *= s.n[a];
+    return (i / stride) % s.n[axis];
+}
+
+// dst = i k_axis src, with the Nyquist mode of i k_axis set to zero.
+template <typename R>
+__global__ void k_deriv(const SpecArgs s, const typename CT<R>::C *__restrict__ src, typename CT<R>::C *__restrict__ dst,
+                        int axis)
+{
+    using C = typename CT<R>::C;
+    const int64_t na = s.n[axis];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = axis_index(i, s, axis);
+        const R k = (2 * j == na) ? (R)0 : (R)(s.kf[axis] * (double)(j < na / 2 ? j : j - na));
+        const C v = src[i];
+        dst[i] = mk(-k * v.y, k * v.x);
+    }
+}
+
+// w <- u = Im(conj(psi) * w / N) / |psi|  (0 where |psi|^2 < 1e-30), stored as (u, 0).
+template <typename R>
+__global__ void k_velocity(const SpecArgs s, const typename CT<R>::C *__restrict__ psi, typename CT<R>::C *__restrict__ w)
+{
+    using C = typename CT<R>::C;
+    const R invn = (R)(1.0 / (double)s.N);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.N; i += (int64_t)gridDim.x * blockDim.x) {
+        const C p = psi[i];
+        const C d = w[i];
+        const R rho = p.x * p.x + p.y * p.y;
+        R u = (R)0;
+        if (rho >= (R)1e-30) u = (p.x * d.y - p.y * d.x) * invn / sqrt(rho);
+        w[i] = mk(u, (R)0);
+    }
+}
+
+// Shell histogram of |u_i|^2 and |u_c|^2 over the k grid, one partial
+// histogram per block (hist[block][2][nshells]).
+template <typename R>
+__global__ void k_bin(const SpecArgs s, const typename CT<R>::C *__restrict__ u0, const typename CT<R>::C *__restrict__ u1,
+                      const typename CT<R>::C *__restrict__ u2, int64_t nshells, double *__restrict__ hist)
+{
+    using C = typename CT<R>::C;
+    extern __shared__ double sh[];   // [2][nshells]
+    for (int64_t i = threadIdx.x; i < 2 * nshells; i += blockDim.x) sh[i] = 0.0;
+    __syncthreads();
+    const C *u[3] = {u0, u1, u2};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.N; i += (int64_t)gridDim.x * blockDim.x) {
+        double kv[3] = {0.0, 0.0, 0.0}, q2 = 0.0, k2 = 0.0;
+        int64_t rem = i;
+        for (int a = 0; a < s.ndim; ++a) {
+            const int64_t j = rem % s.n[a];
+            rem /= s.n[a];
+            const int64_t m = j < s.n[a] / 2 ? j : j - s.n[a];
+            kv[a] = s.kf[a] * (double)m;
+            k2 += kv[a] * kv[a];
+            const double qa = (double)m * s.lratio[a];
+            q2 += qa * qa;
+        }
+        double ur[3] = {0, 0, 0}, ui[3] = {0, 0, 0}, kdr = 0.0, kdi = 0.0;
+        for (int a = 0; a < s.ndim; ++a) {
+            const C v = u[a][i];
+            ur[a] = (double)v.x;
+            ui[a] = (double)v.y;
+            kdr += kv[a] * ur[a];
+            kdi += kv[a] * ui[a];
+        }
+        double ec = 0.0, ei = 0.0;
+        for (int a = 0; a < s.ndim; ++a) {
+            const double cr = k2 > 0.0 ? kv[a] * kdr / k2 : 0.0;
+            const double ci = k2 > 0.0 ? kv[a] * kdi / k2 : 0.0;
+            ec += cr * cr + ci * ci;
+            ei += (ur[a] - cr) * (ur[a] - cr) + (ui[a] - ci) * (ui[a] - ci);
+        }
+        const int64_t sh_i = (int64_t)floor(sqrt(q2) + 0.5);
+        atomicAdd(&sh[sh_i], ei);
+        atomicAdd(&sh[nshells + sh_i], ec);
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < 2 * nshells; i += blockDim.x) hist[(int64_t)blockIdx.x * 2 * nshells + i] = sh[i];
+}
+
+// out[shell] = 1/2 dV/N sum over blocks (in block order) of the partial histograms.
+__global__ void k_hist_reduce(const double *__restrict__ hist, int nblocks, int64_t nshells, double half_dv_over_n,
+                              double *__restrict__ out_inc, double *__restrict__ out_comp)
+{
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= nshells) return;
+    double a = 0.0, c = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        a += hist[(int64_t)b * 2 * nshells + s];
+        c += hist[(int64_t)b * 2 * nshells + nshells + s];
+    }
+    out_inc[s] = half_dv_over_n * a;
+    out_comp[s] = half_dv_over_n * c;
+}
+
+static int grid_for(int64_t N)
+{
+    int64_t b = (N + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+int bin_blocks(const SpecArgs &s)
+{
+    int64_t b = (s.N + 255) / 256;
+    if (b > 152 * 2) b = 152 * 2;
+    return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_deriv(const SpecArgs &s, const void *src, void *dst, int axis, cudaStream_t st)
+{
+    if (s.prec == 0)
+        k_deriv<float><<<grid_for(s.N), 256, 0, st>>>(s, (const float2 *)src, (float2 *)dst, axis);
+    else
+        k_deriv<double><<<grid_for(s.N), 256, 0, st>>>(s, (const double2 *)src, (double2 *)dst, axis);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_velocity(const SpecArgs &s, const void *psi, void *w, cudaStream_t st)
+{
+    if (s.prec == 0)
+        k_velocity<float><<<grid_for(s.N), 256, 0, st>>>(s, (const float2 *)psi, (float2 *)w);
+    else
+        k_velocity<double><<<grid_for(s.N), 256, 0, st>>>(s, (const double2 *)psi, (double2 *)w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const SpecArgs &s, void *const *uh, int64_t nshells, double *block_hist, int nblocks,
+                       cudaStream_t st)
+{
+    const size_t smem = sizeof(double) * 2 * (size_t)nshells;
+    cudaError_t e;
+    if (s.prec == 0) {
+        e = cudaFuncSetAttribute(k_bin<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_bin<float><<<nblocks, 256, smem, st>>>(s, (const float2 *)uh[0], (const float2 *)uh[1],
+                                                 (const float2 *)uh[2], nshells, block_hist);
+    } else {
+        e = cudaFuncSetAttribute(k_bin<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_bin<double><<<nblocks, 256, smem, st>>>(s, (const double2 *)uh[0], (const double2 *)uh[1],
+                                                  (const double2 *)uh[2], nshells, block_hist);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_reduce(const double *block_hist, int nblocks, int64_t nshells, double dv_over_n,
+                               double *out_inc, double *out_comp, cudaStream_t st)
+{
+    const int nb = (int)((nshells + 127) / 128);
+    k_hist_reduce<<<nb, 128, 0, st>>>(block_hist, nblocks, nshells, 0.5 * dv_over_n, out_inc, out_comp);
+    return cudaGetLastError();
+}
+
+}  // namespace gpe

@@ -1,0 +1,258 @@
+// fft_tile.cuh - register/shared-memory Stockham FFT engine for tiles of lines.
+//
+// A CTA owns a tile of L lines of N = 2^p complex points.  Each thread holds
+// E = min(8, N) points of one line in registers: point index i = tl + TPL*e
+// (e = 0..E-1, TPL = N/E threads per line).  A transform is a sequence of
+// Stockham passes of radix 2, 4 or 8 (the first pass takes the remainder of
+// log2 N modulo 3).  In every pass the thread's butterflies read exactly the
+// points it holds, so only the outputs of non-final passes go through shared
+// memory; the last pass leaves point tl + TPL*e in register e again.  Two
+// transforms in a row (FFT, pointwise op, IFFT) therefore need no shared-memory
+// round trip between them, and loads/stores to global memory happen straight
+// from registers with consecutive threads on consecutive addresses.
+//
+// The twiddle table holds exp(-2 pi i t / N), t < N (conjugated for inverse
+// transforms).
+//
+// Stockham pass with radix r over sub-transforms of size Ns (Ns = product of the
+// earlier radices): butterfly j (0 <= j < N/r), k = j mod Ns, reads x[j + m N/r],
+// multiplies input m by W^(m k) with W = exp(dir 2 pi i / (Ns r)), takes an r-point
+// DFT and writes output m to y[(j div Ns) Ns r + k + m Ns].
+//
+// Unit-modulus factors (twiddles, phase tables) are applied with a modulus
+// error far below one ulp of the bulk precision.  A unit factor rounded to
+// single precision has |w| = 1 + O(eps); applied to the same data every step,
+// such errors do not average out and the norm drifts by ~1e-5 per thousand
+// steps.  In single precision every table factor is therefore a pair
+// hi + lo of floats (hi = fl(w), lo = fl(w - hi)) and the product v*(hi + lo)
+// is formed with fused multiply-adds so that only the final value is rounded;
+// the constant 1/sqrt(2) of the radix-8 butterfly is carried the same way.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gpe {
+
+// ---------------------------------------------------------------- complex
+template <typename R> struct CT;
+template <> struct CT<float> { using C = float2; };
+template <> struct CT<double> { using C = double2; };
+
+__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b)
+{
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b)
+{
+    return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { return mk(a.x * s, a.y * s); }
+template <typename C> __device__ __forceinline__ auto cabs2(C a) -> decltype(a.x) { return a.x * a.x + a.y * a.y; }
+
+// Table entry of a unit factor: float -> (hi.x, hi.y, lo.x, lo.y), double -> value.
+template <typename R> struct UT;
+template <> struct UT<float> { using U = float4; };
+template <> struct UT<double> { using U = double2; };
+
+// v * u for a unit factor u (conj(u) when CONJ), rounding only the result
+template <bool CONJ = false> __device__ __forceinline__ float2 umul(float2 v, float4 u)
+{
+    const float uy = CONJ ? -u.y : u.y, wy = CONJ ? -u.w : u.w;
+    const float tx = fmaf(v.x, u.z, -v.y * wy);
+    const float ty = fmaf(v.x, wy, v.y * u.z);
+    return mk(fmaf(v.x, u.x, fmaf(-v.y, uy, tx)), fmaf(v.x, uy, fmaf(v.y, u.x, ty)));
+}
+template <bool CONJ = false> __device__ __forceinline__ double2 umul(double2 v, double2 u)
+{
+    const double uy = CONJ ? -u.y : u.y;
+    return mk(fma(v.x, u.x, -v.y * uy), fma(v.x, uy, v.y * u.x));
+}
+
+// v * (1 + w) for a unit factor stored as its offset w from one
+__device__ __forceinline__ float2 cmadd1(float2 v, float2 w)
+{
+    return mk(fmaf(v.x, w.x, fmaf(-v.y, w.y, v.x)), fmaf(v.x, w.y, fmaf(v.y, w.x, v.y)));
+}
+__device__ __forceinline__ double2 cmadd1(double2 v, double2 w)
+{
+    return mk(fma(v.x, w.x, fma(-v.y, w.y, v.x)), fma(v.x, w.y, fma(v.y, w.x, v.y)));
+}
+// offset form of a product of two unit factors: (1+a)(1+b) - 1
+template <typename C> __device__ __forceinline__ C wcomb(C a, C b)
+{
+    return mk(a.x + b.x + (a.x * b.x - a.y * b.y), a.y + b.y + (a.x * b.y + a.y * b.x));
+}
+// x / sqrt(2), with the constant carried to twice the working precision in float
+__device__ __forceinline__ float mul_rsqrt2(float x)
+{
+    const float hi = 0.707106769084930419921875f, lo = 1.2101617e-08f;
+    return fmaf(x, hi, x * lo);
+}
+__device__ __forceinline__ double mul_rsqrt2(double x) { return x * 0.70710678118654752440; }
+
+// multiply by dir*i  (dir = -1: -i, dir = +1: +i)
+template <int DIR, typename C> __device__ __forceinline__ C mul_i(C a)
+{
+    if (DIR < 0) return mk(a.y, -a.x);
+    return mk(-a.y, a.x);
+}
+
+// a * exp(DIR * 2 pi i * K / M) for M <= 16 with K a compile-time constant
+// after unrolling; cos/sin of multiples of pi/8 written out.
+template <int M, int DIR, typename C> __device__ __forceinline__ C twc(C a, int K)
+{
+    using R = decltype(a.x);
+    const int idx = (K * (16 / M)) & 15;
+    if (idx == 0) return a;
+    if (idx == 4) return mul_i<DIR>(a);
+    if (idx == 8) return mk(-a.x, -a.y);
+    if (idx == 12) return mul_i<-DIR>(a);
+    if (idx == 2 || idx == 6 || idx == 10 || idx == 14) {
+        // (+-1 +- i)/sqrt(2): exp(DIR i pi idx/8) = (cx + i sy DIR)/sqrt(2)
+        const R cx = (idx == 2 || idx == 14) ? (R)1 : (R)-1;
+        const R sy = ((idx == 2 || idx == 6) ? (R)1 : (R)-1) * (R)DIR;
+        return mk(mul_rsqrt2(cx * a.x - sy * a.y), mul_rsqrt2(sy * a.x + cx * a.y));
+    }
+    // cos(2 pi idx / 16), sin(2 pi idx / 16)
+    const R c1 = (R)0.92387953251128675613, s1 = (R)0.38268343236508977173, h = (R)0.70710678118654752440;
+    R c, s;
+    switch (idx) {
+    case 1: c = c1; s = s1; break;
+    case 2: c = h; s = h; break;
+    case 3: c = s1; s = c1; break;
+    case 5: c = -s1; s = c1; break;
+    case 6: c = -h; s = h; break;
+    case 7: c = -c1; s = s1; break;
+    case 9: c = -c1; s = -s1; break;
+    case 10: c = -h; s = -h; break;
+    case 11: c = -s1; s = -c1; break;
+    case 13: c = s1; s = -c1; break;
+    case 14: c = h; s = -h; break;
+    default: c = c1; s = -s1; break;   // 15
+    }
+    if (DIR < 0) s = -s;
+    return mk(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+// In-register DFT of size M (1, 2, 4, 8, 16): even/odd split (radix-2 DIT),
+// natural-order input and output.  DIR = -1 forward, +1 inverse.
+template <int M, int DIR, typename C> struct Dft {
+    __device__ __forceinline__ static void run(C *x)
+    {
+        C e[M / 2], o[M / 2];
+#pragma unroll
+        for (int i = 0; i < M / 2; ++i) { e[i] = x[2 * i]; o[i] = x[2 * i + 1]; }
+        Dft<M / 2, DIR, C>::run(e);
+        Dft<M / 2, DIR, C>::run(o);
+#pragma unroll
+        for (int k = 0; k < M / 2; ++k) {
+            C t = twc<M, DIR>(o[k], k);
+            x[k] = cadd(e[k], t);
+            x[k + M / 2] = csub(e[k], t);
+        }
+    }
+};
+template <int DIR, typename C> struct Dft<1, DIR, C> {
+    __device__ __forceinline__ static void run(C *) {}
+};
+template <int DIR, typename C> struct Dft<2, DIR, C> {
+    __device__ __forceinline__ static void run(C *x)
+    {
+        C a = x[0], b = x[1];
+        x[0] = cadd(a, b);
+        x[1] = csub(a, b);
+    }
+};
+
+// ---------------------------------------------------------------- pass plan
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+
+template <int N> struct Radix {
+    static constexpr int LG = ilog2c(N);
+    static constexpr int E = N >= 8 ? 8 : N;           // points per thread
+    static constexpr int REM = N >= 8 ? LG % 3 : 0;    // log2 of the first pass when not 8
+    static constexpr int P = N < 8 ? 1 : LG / 3 + (REM ? 1 : 0);
+    __host__ __device__ static constexpr int radix(int p) { return N < 8 ? N : ((REM && p == 0) ? (1 << REM) : 8); }
+    __host__ __device__ static constexpr int ns(int p) { return p == 0 ? 1 : ns(p - 1) * radix(p - 1); }
+};
+
+// ---------------------------------------------------------------- tile engine
+// ROWS = true : lines are contiguous rows (x axis); shared layout row-major with
+//               one pad point every 8 points (keeps stride-r writes conflict-free).
+// ROWS = false: lines are strided (y or z axis); L lines interleaved point by point.
+template <typename R, int N, int L, bool ROWS> struct Tile {
+    using C = typename CT<R>::C;
+    static constexpr int E = Radix<N>::E;
+    static constexpr int TPL = N / E;
+    static constexpr int NT = L * TPL;
+    static constexpr int PADN = N + N / 8;
+    static constexpr int SMEM_POINTS = ROWS ? L * PADN : N * L;
+
+    __device__ __forceinline__ static int sidx(int i, int l)
+    {
+        if (ROWS) return l * PADN + i + (i >> 3);
+        return i * L + l;
+    }
+    __device__ __forceinline__ static int line_of(int t) { return ROWS ? t / TPL : t % L; }
+    __device__ __forceinline__ static int tl_of(int t) { return ROWS ? t % TPL : t / L; }
+
+    using U = typename UT<R>::U;
+
+    // One pass p of the transform.  v holds points tl + TPL*e.
+    template <int DIR, int p>
+    __device__ __forceinline__ static void pass(C (&v)[E], C *sm, int tl, int l, const U *__restrict__ tw)
+    {
+        constexpr int r = Radix<N>::radix(p);
+        constexpr int Ns = Radix<N>::ns(p);
+        constexpr int B = E / r;
+        constexpr bool last = (p == Radix<N>::P - 1);
+        if constexpr (p > 0) {
+            __syncthreads();                          // previous pass outputs visible
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = sm[sidx(tl + TPL * e, l)];
+            if constexpr (!last) __syncthreads();     // all reads done before rewriting
+        } else if constexpr (!last) {
+            __syncthreads();                          // earlier readers of sm are done
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            const int j = tl + q * TPL;
+            const int k = j & (Ns - 1);
+            C x[r];
+#pragma unroll
+            for (int m = 0; m < r; ++m) x[m] = v[q + m * B];
+            if constexpr (Ns > 1) {
+#pragma unroll
+                for (int m = 1; m < r; ++m) x[m] = umul<(DIR > 0)>(x[m], tw[m * k * (N / (Ns * r))]);
+            }
+            Dft<r, DIR, C>::run(x);
+            if constexpr (last) {
+#pragma unroll
+                for (int m = 0; m < r; ++m) v[q + m * B] = x[m];
+            } else {
+                const int base = (j / Ns) * Ns * r + k;
+#pragma unroll
+                for (int m = 0; m < r; ++m) sm[sidx(base + m * Ns, l)] = x[m];
+            }
+        }
+    }
+
+    // Full N-point transform of the thread's line, in place in registers.
+    // DIR = -1 forward (unnormalised), +1 inverse (unnormalised).
+    template <int DIR, int p = 0>
+    __device__ __forceinline__ static void fft(C (&v)[E], C *sm, int tl, int l, const U *tw)
+    {
+        if constexpr (p < Radix<N>::P) {
+            pass<DIR, p>(v, sm, tl, l, tw);
+            fft<DIR, p + 1>(v, sm, tl, l, tw);
+        }
+    }
+};
+
+}  // namespace gpe

@@ -1,0 +1,110 @@
+// gpe_internal.h - launch descriptors shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gpe {
+
+// pointwise operations a pass applies to every point it holds
+enum PointOp : int {
+    OP_NONE = 0,
+    OP_NREAL = 1,        // psi *= Vphase(x) exp(-i g c |psi|^2)        (real-time nonlinear substep)
+    OP_NIMAG = 2,        // psi *= Vdecay(x) exp(-g c |psi|^2)          (imaginary-time nonlinear substep)
+    OP_KREAL = 3,        // psi *= prod_a exp(-i k_a^2 dt/2)/n_a          (real-time kinetic substep)
+    OP_KIMAG = 4,        // psi *= prod_a exp(-k_a^2 dt/2)/n_a            (imaginary-time kinetic substep)
+    OP_SCALE_NIMAG = 5,  // psi *= s[instance], then OP_NIMAG            (deferred renormalisation)
+    OP_SCALE = 6,        // psi *= s[instance]
+};
+
+// reductions a pass can produce, one value per line per quantity
+enum PassReduce : int {
+    RED_NONE = 0,
+    RED_NORM = 1,    // q0 = sum |psi|^2 of the final point values
+    RED_DIAG_X = 2,  // x rows: q0 sum rho, q1 sum x^2 rho, q2 sum y^2 rho, q3 sum z^2 rho,
+                     //         q4 sum V rho, q5 sum rho^2, q6 sum kx^2 |F_x psi|^2 (no store)
+    RED_DIAG_K = 3,  // y or z lines: q(6+axis) sum k^2 |F_axis psi|^2 (no store)
+};
+
+enum { NQ = 9 };     // reduction quantities per line
+
+struct PassArgs {
+    const void *src;
+    void *dst;
+    int64_t ntiles;        // tiles of L lines
+    int64_t lines_total;   // batch * lines per instance
+    int lg_lpi;            // log2(lines per instance)
+    int lg_A;              // line li starts at (li & (A-1)) + (li >> lg_A) * Sb
+    int64_t Sb;
+    int64_t estride;       // element stride along the line
+    int64_t inst_stride;   // elements between instances
+    int lg_o0;             // other-axis coordinates: c0 = li & (o0n-1), c1 = li >> lg_o0
+    int o0n, o1n;          // sizes of the other axes (1 if absent)
+    int nax;               // points on this axis
+    int axis;              // 0, 1, 2
+    int op_pre, fft1, op_mid, fft2, op_post, red;   // fft: 0 none, -1 forward, +1 inverse
+    // unit-factor tables: double2 values (complex128) or float4 hi/lo pairs (complex64)
+    const void *tw;        // exp(-2 pi i t / nax), t < nax
+    // trap tables per instance ([batch][n]); NULL when the trap is off on that axis
+    const void *vt_ax, *vt_o0, *vt_o1;   // unit factors exp(-i V_a c)
+    const void *vi_ax, *vi_o0, *vi_o1;   // real    exp(-V_a c)
+    // kinetic tables ([n]); NULL when absent (1D/2D other axes)
+    const void *kt_ax, *kt_o0, *kt_o1;   // unit factors exp(-i k_a^2 dt/2)
+    const void *ki_ax, *ki_o0, *ki_o1;   // real
+    const double *g;       // per-instance interaction
+    double nl_c;           // theta = g * nl_c * |psi|^2
+    double inv_n;          // 1/N applied with the kinetic substep
+    const double *scale;   // per-instance renormalisation factor
+    double *partials;      // [NQ][lines_cap] per-line sums
+    int64_t lines_cap;
+    // diagnostics geometry
+    const double *gamma;   // [batch][3]
+    double lo[3], h[3], kf[3];   // box corner, spacing, 2 pi / len per axis
+};
+
+// launch one pass; returns cudaSuccess or the launch error
+cudaError_t launch_pass(int prec, bool rows, const PassArgs &a, cudaStream_t st);
+int pass_lines_per_tile(int prec, bool rows, int n);
+
+// whole 1D steps with each line (instance) resident on chip for all steps
+struct Line1DArgs {
+    void *psi;
+    int64_t batch;
+    int n;
+    int64_t nsteps;
+    int imag;               // 0 real time, 1 imaginary time with per-step renormalisation
+    const void *tw;
+    const void *kt;         // unit factors exp(-i k^2 dt/2) (real time) or exp(-k^2 dt/2)/n (imag)
+    const void *vh, *vf;    // unit factors exp(-i V dt/2), exp(-i V dt) ([batch][n]) or NULL
+    const void *vi;         // real decay table (imag) or NULL
+    const double *g;
+    double dt;
+    double target_norm_over_dv;   // imag: target norm / cell volume
+    int *err;               // set to 1 if a norm turns non-finite or zero
+};
+cudaError_t launch_line1d(int prec, const Line1DArgs &a, cudaStream_t st);
+
+// reductions and spectra (diag_spec.cu)
+cudaError_t launch_reduce_lines(const double *partials, int64_t lines_cap, int nq_first, int nq,
+                                int64_t batch, int64_t lines_per_inst, double *sums, cudaStream_t st);
+cudaError_t launch_finish_scale(const double *sums, int64_t batch, double dv, double target,
+                                double *scale, int *err, cudaStream_t st);
+cudaError_t launch_finish_diag(const double *sums, int64_t batch, int ndim, const int64_t *n, double dv,
+                               const double *g, double *out6, double *out4, cudaStream_t st);
+
+struct SpecArgs {
+    int prec;
+    int ndim;
+    int64_t n[3];
+    double kf[3];       // 2 pi / len
+    double lratio[3];   // max_len / len
+    int64_t N;
+};
+cudaError_t launch_deriv(const SpecArgs &s, const void *src, void *dst, int axis, cudaStream_t st);
+cudaError_t launch_velocity(const SpecArgs &s, const void *psi, void *w, cudaStream_t st);
+cudaError_t launch_bin(const SpecArgs &s, void *const *uh, int64_t nshells, double *block_hist,
+                       int nblocks, cudaStream_t st);
+cudaError_t launch_hist_reduce(const double *block_hist, int nblocks, int64_t nshells, double dv_over_n,
+                               double *out_inc, double *out_comp, cudaStream_t st);
+int bin_blocks(const SpecArgs &s);
+
+}  // namespace gpe
