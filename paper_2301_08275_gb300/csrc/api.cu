@@ -1,11 +1,11 @@
 // api.cu - plan objects and the C ABI entry points declared in include/gpe.h.
 //
 // A plan holds, per axis, the twiddle table exp(-2 pi i t/n), the kinetic
-// substep tables exp(-i k^2 dt/2) (real time) and exp(-k^2 dt/2)/n
-// (imaginary time), and per instance the trap tables exp(-i V_a dt/2),
-// exp(-i V_a dt) and exp(-V_a dt/2) with V_a = gamma_a^2 x^2 / 2.  All are
-// evaluated in double precision on the host; in single precision the unit
-// factors are stored as hi + lo float pairs (see fft_tile.cuh).  Because the
+// substep table exp(-i k^2 dt/2) - 1 (real time) and exp(-k^2 dt/2)/n
+// (imaginary time), and per instance the trap tables exp(-i V_a dt/2) - 1,
+// exp(-i V_a dt) - 1 and exp(-V_a dt/2) with V_a = gamma_a^2 x^2 / 2.  All are
+// evaluated in double precision on the host; in single precision the complex
+// entries are stored as hi + lo float pairs (see fft_tile.cuh).  Because the
 // trap is separable, V enters every nonlinear substep as a product of per-axis
 // unit phases and only the g|psi|^2 part of the angle is evaluated per point.
 #include <math.h>
@@ -248,7 +248,8 @@ extern "C" gpe_status gpe_plan_create(const gpe_plan_desc *d, void *cuda_stream,
             const int64_t m = t < na / 2 ? t : t - na;
             const double k = p->kf[a] * (double)m;
             const double th = 0.5 * k * k * p->dt;
-            kt[2 * t] = cos(th);
+            // offset exp(-i th) - 1 = (-2 sin^2(th/2), -sin th)
+            kt[2 * t] = -2.0 * sin(0.5 * th) * sin(0.5 * th);
             kt[2 * t + 1] = -sin(th);
             ki[t] = exp(-th) / (double)na;
         }
@@ -263,9 +264,9 @@ extern "C" gpe_status gpe_plan_create(const gpe_plan_desc *d, void *cuda_stream,
                     const double x = p->lo[a] + (double)j * p->h[a];
                     const double V = 0.5 * ga * ga * x * x;
                     const double th = V * p->dt;
-                    vh[2 * (b * na + j)] = cos(0.5 * th);
+                    vh[2 * (b * na + j)] = -2.0 * sin(0.25 * th) * sin(0.25 * th);
                     vh[2 * (b * na + j) + 1] = -sin(0.5 * th);
-                    vf[2 * (b * na + j)] = cos(th);
+                    vf[2 * (b * na + j)] = -2.0 * sin(0.5 * th) * sin(0.5 * th);
                     vf[2 * (b * na + j) + 1] = -sin(th);
                     vi[b * na + j] = exp(-0.5 * th);
                 }

@@ -27,6 +27,8 @@
 // hi + lo of floats (hi = fl(w), lo = fl(w - hi)) and the product v*(hi + lo)
 // is formed with fused multiply-adds so that only the final value is rounded;
 // the constant 1/sqrt(2) of the radix-8 butterfly is carried the same way.
+// Factors whose angle is small where the data lives (kinetic and trap phases,
+// the nonlinear phase) are held as offsets from one instead (cmadd1, uomul).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -74,15 +76,26 @@ template <bool CONJ = false> __device__ __forceinline__ double2 umul(double2 v, 
     return mk(fma(v.x, u.x, -v.y * uy), fma(v.x, uy, v.y * u.x));
 }
 
-// v * (1 + w) for a unit factor stored as its offset w from one
+// v * (1 + w) for a unit factor close to one, stored as its offset w: the
+// small product v*w is formed first and v is added last, so each component is
+// rounded once after the dominant term enters (rounding v*cos first and adding
+// v*sin afterwards would drop the small term in a biased way).
 __device__ __forceinline__ float2 cmadd1(float2 v, float2 w)
 {
-    return mk(fmaf(v.x, w.x, fmaf(-v.y, w.y, v.x)), fmaf(v.x, w.y, fmaf(v.y, w.x, v.y)));
+    return mk(v.x + fmaf(v.x, w.x, -v.y * w.y), v.y + fmaf(v.x, w.y, v.y * w.x));
 }
 __device__ __forceinline__ double2 cmadd1(double2 v, double2 w)
 {
-    return mk(fma(v.x, w.x, fma(-v.y, w.y, v.x)), fma(v.x, w.y, fma(v.y, w.x, v.y)));
+    return mk(v.x + fma(v.x, w.x, -v.y * w.y), v.y + fma(v.x, w.y, v.y * w.x));
 }
+// same with the offset held as a hi + lo float pair (table entries)
+__device__ __forceinline__ float2 uomul(float2 v, float4 w)
+{
+    const float tx = fmaf(v.x, w.z, -v.y * w.w);
+    const float ty = fmaf(v.x, w.w, v.y * w.z);
+    return mk(v.x + fmaf(v.x, w.x, fmaf(-v.y, w.y, tx)), v.y + fmaf(v.x, w.y, fmaf(v.y, w.x, ty)));
+}
+__device__ __forceinline__ double2 uomul(double2 v, double2 w) { return cmadd1(v, w); }
 // offset form of a product of two unit factors: (1+a)(1+b) - 1
 template <typename C> __device__ __forceinline__ C wcomb(C a, C b)
 {

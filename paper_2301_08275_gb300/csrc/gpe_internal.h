@@ -45,10 +45,10 @@ struct PassArgs {
     // unit-factor tables: double2 values (complex128) or float4 hi/lo pairs (complex64)
     const void *tw;        // exp(-2 pi i t / nax), t < nax
     // trap tables per instance ([batch][n]); NULL when the trap is off on that axis
-    const void *vt_ax, *vt_o0, *vt_o1;   // unit factors exp(-i V_a c)
+    const void *vt_ax, *vt_o0, *vt_o1;   // offsets exp(-i V_a c) - 1
     const void *vi_ax, *vi_o0, *vi_o1;   // real    exp(-V_a c)
     // kinetic tables ([n]); NULL when absent (1D/2D other axes)
-    const void *kt_ax, *kt_o0, *kt_o1;   // unit factors exp(-i k_a^2 dt/2)
+    const void *kt_ax, *kt_o0, *kt_o1;   // offsets exp(-i k_a^2 dt/2) - 1
     const void *ki_ax, *ki_o0, *ki_o1;   // real
     const double *g;       // per-instance interaction
     double nl_c;           // theta = g * nl_c * |psi|^2
@@ -73,8 +73,8 @@ struct Line1DArgs {
     int64_t nsteps;
     int imag;               // 0 real time, 1 imaginary time with per-step renormalisation
     const void *tw;
-    const void *kt;         // unit factors exp(-i k^2 dt/2) (real time) or exp(-k^2 dt/2)/n (imag)
-    const void *vh, *vf;    // unit factors exp(-i V dt/2), exp(-i V dt) ([batch][n]) or NULL
+    const void *kt;         // offsets exp(-i k^2 dt/2) - 1 (real time) or exp(-k^2 dt/2)/n (imag)
+    const void *vh, *vf;    // offsets exp(-i V dt/2) - 1, exp(-i V dt) - 1 ([batch][n]) or NULL
     const void *vi;         // real decay table (imag) or NULL
     const double *g;
     double dt;

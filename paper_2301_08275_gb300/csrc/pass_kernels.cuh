@@ -67,7 +67,7 @@ __device__ __forceinline__ void point_op(int op, typename CT<R>::C (&v)[E], cons
     if (op == OP_NONE) return;
     using U = typename UT<R>::U;
     if (op == OP_KREAL) {
-        // tables hold exp(-i k_a^2 dt/2); the 1/N of the inverse transform is exact
+        // tables hold exp(-i k_a^2 dt/2) - 1; the 1/N of the inverse transform is exact
         const U *kt = static_cast<const U *>(a.kt_ax);
         const U *k0 = static_cast<const U *>(a.kt_o0);
         const U *k1 = static_cast<const U *>(a.kt_o1);
@@ -75,9 +75,9 @@ __device__ __forceinline__ void point_op(int op, typename CT<R>::C (&v)[E], cons
         const R invn = (R)a.inv_n;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            C x = umul(v[e], kt[tl + TPL * e]);
-            if (k0) x = umul(x, f0);
-            if (k1) x = umul(x, f1);
+            C x = uomul(v[e], kt[tl + TPL * e]);
+            if (k0) x = uomul(x, f0);
+            if (k1) x = uomul(x, f1);
             v[e] = cscale(x, invn);
         }
         return;
@@ -99,7 +99,7 @@ __device__ __forceinline__ void point_op(int op, typename CT<R>::C (&v)[E], cons
     }
     const R gc = (R)(a.g[inst] * a.nl_c);
     if (op == OP_NREAL) {
-        // trap tables hold exp(-i V_a c)
+        // trap tables hold exp(-i V_a c) - 1
         const U *vax = static_cast<const U *>(a.vt_ax);
         const U *v0 = static_cast<const U *>(a.vt_o0);
         const U *v1 = static_cast<const U *>(a.vt_o1);
@@ -108,9 +108,9 @@ __device__ __forceinline__ void point_op(int op, typename CT<R>::C (&v)[E], cons
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             C x = cmadd1(v[e], phase_offset(gc * cabs2(v[e])));
-            if (vax) x = umul(x, vax[(int64_t)inst * a.nax + tl + TPL * e]);
-            if (v0) x = umul(x, f0);
-            if (v1) x = umul(x, f1);
+            if (vax) x = uomul(x, vax[(int64_t)inst * a.nax + tl + TPL * e]);
+            if (v0) x = uomul(x, f0);
+            if (v1) x = uomul(x, f1);
             v[e] = x;
         }
         return;
@@ -269,13 +269,13 @@ __global__ void __launch_bounds__(Tile<R, N, L, true>::NT) k_line1d(const Line1D
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 v[e] = cmadd1(v[e], phase_offset(gh * cabs2(v[e])));
-                if (vh) v[e] = umul(v[e], vh[ib * N + tl + TPL * e]);
+                if (vh) v[e] = uomul(v[e], vh[ib * N + tl + TPL * e]);
             }
 #pragma unroll 1
             for (int64_t st = 0; st < a.nsteps; ++st) {
                 T::template fft<-1>(v, sm, tl, l, tw);
 #pragma unroll
-                for (int e = 0; e < E; ++e) v[e] = cscale(umul(v[e], kt[tl + TPL * e]), invn);
+                for (int e = 0; e < E; ++e) v[e] = cscale(uomul(v[e], kt[tl + TPL * e]), invn);
                 T::template fft<1>(v, sm, tl, l, tw);
                 const bool last = (st == a.nsteps - 1);
                 const R gc = last ? gh : gf;
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(Tile<R, N, L, true>::NT) k_line1d(const Line1D
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     v[e] = cmadd1(v[e], phase_offset(gc * cabs2(v[e])));
-                    if (vt) v[e] = umul(v[e], vt[ib * N + tl + TPL * e]);
+                    if (vt) v[e] = uomul(v[e], vt[ib * N + tl + TPL * e]);
                 }
             }
         } else {
