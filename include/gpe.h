@@ -142,6 +142,25 @@ int gpe_trace_count(gpe_plan *plan);
 gpe_status gpe_trace_read(gpe_plan *plan, int i, char *name, size_t name_len, int64_t *launches,
                           double *total_ms);
 
+/* Norm and energy without any allocation (the paper has no counterpart; this
+ * exists for callers that cannot allocate).  Some callers cannot call
+ * cudaMalloc: code that runs under a framework owning all device memory through
+ * its own allocator, and latency-critical loops where cudaMalloc/cudaFree
+ * would synchronise the device.  For one instance described by desc (batch
+ * must be 1; g_each and gamma_each are ignored) this computes the six values
+ * of gpe_norm_energy into out_host[0..5] using only psi_dev, out_host and a
+ * fixed device array of about 2.4 MiB that every GPU loading the library
+ * holds until the process exits; it calls no allocating routine.
+ * Limit: N / n[a] <= GPE_NOALLOC_MAX_LINES on every axis (for example 1024^2,
+ * 4096 x 32, 128^3); larger grids are rejected with GPE_EUNSUPPORTED.
+ * The first call made on a device looks up the array's device address there
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call reuses the same array, so calls that overlap on the GPU (from
+ * other streams or threads) race: serialise them.  Synchronises cuda_stream. */
+#define GPE_NOALLOC_MAX_LINES 32768
+gpe_status gpe_norm_energy_noalloc(const gpe_plan_desc *desc, const void *psi_dev, void *cuda_stream,
+                                   double *out_host);
+
 /* Thread-local message describing the last error (never NULL). */
 const char *gpe_last_error(void);
 

@@ -28,7 +28,7 @@ STATUS = {0: "GPE_OK", 1: "GPE_EINVAL", 2: "GPE_EUNSUPPORTED", 3: "GPE_ENOMEM", 
 
 EXPORTS = ["gpe_plan_create", "gpe_plan_destroy", "gpe_step_real", "gpe_step_real_host", "gpe_step_imag",
            "gpe_norm_energy", "gpe_rms_size", "gpe_spectrum_nshells", "gpe_spectrum", "gpe_last_error",
-           "gpe_trace_enable", "gpe_trace_count", "gpe_trace_read"]
+           "gpe_trace_enable", "gpe_trace_count", "gpe_trace_read", "gpe_norm_energy_noalloc"]
 
 
 class GpeError(RuntimeError):
@@ -81,6 +81,7 @@ def lib():
         L.gpe_spectrum_nshells.restype = i64
         L.gpe_spectrum.argtypes = [vp, vp, ctypes.c_uint, dp, i64]
         L.gpe_last_error.restype = ctypes.c_char_p
+        L.gpe_norm_energy_noalloc.argtypes = [ctypes.POINTER(gpe_plan_desc), vp, vp, dp]
         L.gpe_trace_enable.argtypes = [vp, ctypes.c_int]
         L.gpe_trace_count.argtypes = [vp]
         L.gpe_trace_read.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t,
@@ -154,6 +155,15 @@ def gpe_spectrum(plan, psi_ptr, kinds, batch):
     out = np.zeros(nk * batch * ns)
     _check(lib().gpe_spectrum(plan, ctypes.c_void_p(psi_ptr), int(kinds), _dptr(out), ns))
     return out.reshape(nk, batch, ns)
+
+
+def gpe_norm_energy_noalloc(desc, psi_ptr, stream=None):
+    """Norm/energy of one instance without any allocation by the library
+    (see include/gpe.h); returns [norm, E_kin, E_pot, E_int, E, mu]."""
+    out = np.zeros(6)
+    _check(lib().gpe_norm_energy_noalloc(ctypes.byref(desc), ctypes.c_void_p(psi_ptr),
+                                         ctypes.c_void_p(stream or 0), _dptr(out)))
+    return out
 
 
 def gpe_trace_enable(plan, enable=True):

@@ -69,6 +69,8 @@ static gpe_status fail(gpe_status s, const std::string &msg)
 
 extern "C" const char *gpe_last_error(void) { return g_last_error.c_str(); }
 
+void gpe::set_last_error(const char *msg) { g_last_error = msg; }
+
 // ------------------------------------------------------------------ plan
 struct gpe_plan {
     int ndim = 0;

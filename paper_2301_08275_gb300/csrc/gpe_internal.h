@@ -61,6 +61,9 @@ struct PassArgs {
     double lo[3], h[3], kf[3];   // box corner, spacing, 2 pi / len per axis
 };
 
+// record the thread-local message returned by gpe_last_error()
+void set_last_error(const char *msg);
+
 // launch one pass; returns cudaSuccess or the launch error
 cudaError_t launch_pass(int prec, bool rows, const PassArgs &a, cudaStream_t st);
 int pass_lines_per_tile(int prec, bool rows, int n);
