@@ -138,6 +138,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, device=None):
+    """Maximum of a per-rank float over the process group (the identity on one
+    process).  Used for the timed region: the job takes as long as its slowest
+    rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -249,12 +262,7 @@ def run_ours(args, key, wl):
         plan.step_real(psi, args.steps)
         ev1.record(stream)
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
     value = ws * spec.N * args.steps / (ms / 1e3)
 
     # per-kernel timing over a second timed region of the same length, traced
@@ -288,12 +296,7 @@ def run_ours(args, key, wl):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         plan.step_real_host(hnp, 1)
-    el = time.perf_counter() - t0
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([el], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(time.perf_counter() - t0, dev)
     state_bytes = spec.N * (8 if prec == gpe.GPE_C64 else 16)
     e2e = {"value": ws * spec.N * e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
            "d2h_bytes_per_step": state_bytes, "steps": e2e_steps,
@@ -325,18 +328,135 @@ def run_ours(args, key, wl):
     return 0
 
 
+def run_batched(args):
+    """512 uneven 2D instances (64^2..512^2, g in [0,1000], traps gamma in [1,4]),
+    500 real-time steps: one graph-captured batch call versus sequential
+    per-instance stepping with the same kernels."""
+    import torch
+    import paper_2301_08275_gb300 as gpe
+    gpe.build()
+    torch.cuda.set_device(0)
+    count = args.instances
+    items = gi.batched_specs(count=count, seed=0)
+    steps = args.steps
+    stream = torch.cuda.Stream()
+    xs = [torch.from_numpy(psi.astype(np.complex64)).cuda() for _, psi in items]
+    descs = [gpe.make_desc(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma, prec=gpe.GPE_C64)[0]
+             for sp, _ in items]
+    torch.cuda.synchronize()
+    b = gpe.gpe_batch_create(descs, stream.cuda_stream)
+    ptrs = [x.data_ptr() for x in xs]
+    gpe.gpe_batch_step_real(b, ptrs, args.warmup, True)
+    gpe.gpe_batch_step_real(b, ptrs, steps, True)          # capture
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    gpe.gpe_batch_step_real(b, ptrs, steps, True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = ev0.elapsed_time(ev1) / 1e3
+    pts = sum(sp.N for sp, _ in items)
+    # sequential: one plan per instance, stepped one after another
+    plans = [gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma, prec=gpe.GPE_C64, stream=stream)
+             for sp, _ in items]
+    for p, x in zip(plans, xs):
+        p.step_real(x, args.warmup)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for p, x in zip(plans, xs):
+        p.step_real(x, steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = ev0.elapsed_time(ev1) / 1e3
+    e = gpe.gpe_batch_norm_energy(b, ptrs)
+    line = {"metric": "batched TSSP grid-point updates/s", "value": pts * steps / t_batch, "unit": UNIT,
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": t_batch / steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%d uneven 2D instances 64^2..512^2, [-12,12)^2, g~U[0,1000], gamma~U[1,4], "
+                                   "complex64" % count, "groups": gpe.gpe_batch_groups(b), "points": pts},
+            "sequential": {"value": pts * steps / t_seq, "ms_per_step": t_seq / steps * 1e3,
+                           "how": "one plan per instance, gpe_step_real(%d) one after another" % steps},
+            "speedup_vs_sequential": t_seq / t_batch, "finite": bool(np.all(np.isfinite(e)))}
+    print(json.dumps(line), flush=True)
+    gpe.gpe_batch_destroy(b)
+    return 0
+
+
+def run_serving(args):
+    """Poisson stream (mean 200 requests/s) of mixed 1D/2D/3D solves, real and
+    imaginary time, through the request server; p50/p99 latency and aggregate
+    grid-point updates/s."""
+    import torch
+    import paper_2301_08275_gb300 as gpe
+    gpe.build()
+    torch.cuda.set_device(0)
+    items = gi.request_stream(count=args.requests, rate=200.0, seed=0, max2d=args.max2d, max3d=args.max3d)
+    srv = gpe.gpe_server_create(150 * 10 ** 9, max_active=args.max_active, chunk_steps=64)
+    tickets = []
+    t0 = time.perf_counter()
+    states = {}
+    for i, it in enumerate(items):
+        sp = it["spec"]
+        while time.perf_counter() - t0 < it["t"]:
+            time.sleep(min(0.001, it["t"] - (time.perf_counter() - t0)))
+        psi = gi.harmonic_gaussian(sp, seed=it["seed"], noise=0.01).astype(np.complex64)
+        states[i] = psi
+        d = gpe.make_desc(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma, prec=gpe.GPE_C64)[0]
+        tickets.append(gpe.gpe_serve_submit(srv, d, psi, imag=(it["mode"] == "imag"), nsteps=it["steps"],
+                                            etol=it["etol"], check_every=50))
+    lat, upd, fails = [], 0.0, 0
+    for i, t in enumerate(tickets):
+        r = gpe.gpe_serve_poll(srv, t, timeout_ms=-1)
+        if r.status != 0:
+            fails += 1
+            continue
+        lat.append(r.t_done - r.t_submit)
+        upd += items[i]["spec"].N * r.steps_done
+    wall = time.perf_counter() - t0
+    gpe.gpe_server_destroy(srv)
+    lat = np.array(lat)
+    line = {"metric": "served GPE solves: p50/p99 latency and aggregate updates/s",
+            "value": float(np.percentile(lat, 50)) if len(lat) else None, "unit": "s (p50 latency)",
+            "p99_s": float(np.percentile(lat, 99)) if len(lat) else None, "updates_per_s": upd / wall,
+            "requests": len(items), "failed": fails, "wall_s": wall, "higher_is_better": False, "n_gpus": 1,
+            "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "Poisson 200 req/s; 1D 4096, 2D 256^2..%d^2, 3D 64^3..%d^3; real 100-2000 steps "
+                                   "or imaginary time to |dE|<1e-9 (checked every 50 steps); budget 150 GB"
+                                   % (args.max2d, args.max3d), "max_active": args.max_active}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tg512", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="tg512", choices=sorted(WORKLOADS) + ["batched", "serving"])
+    ap.add_argument("--instances", type=int, default=512, help="batched: number of instances")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
+    ap.add_argument("--max-active", type=int, default=32, help="serving: resident requests")
+    ap.add_argument("--max2d", type=int, default=2048, help="serving: largest 2D grid side")
+    ap.add_argument("--max3d", type=int, default=256, help="serving: largest 3D grid side")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--grid", default=None,
+                    help="override the workload grid, e.g. 512,512,128 (profiling cases; same box and parameters)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    wl = WORKLOADS[args.workload]
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
+    wl = dict(WORKLOADS[args.workload])
+    if args.grid:
+        sp = wl["spec"]
+        n = tuple(int(v) for v in args.grid.split(","))
+        if len(n) != sp.ndim:
+            raise SystemExit("--grid needs %d sizes" % sp.ndim)
+        wl["spec"] = gi.Spec(n=n, lo=sp.lo, length=sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma)
+        wl["name"] = wl["name"] + " [grid overridden to %s]" % "x".join(map(str, n))
     if args.impl == "reference":
         return run_reference(args, args.workload, wl)
     return run_ours(args, args.workload, wl)

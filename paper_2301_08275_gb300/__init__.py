@@ -28,7 +28,10 @@ STATUS = {0: "GPE_OK", 1: "GPE_EINVAL", 2: "GPE_EUNSUPPORTED", 3: "GPE_ENOMEM", 
 
 EXPORTS = ["gpe_plan_create", "gpe_plan_destroy", "gpe_step_real", "gpe_step_real_host", "gpe_step_imag",
            "gpe_norm_energy", "gpe_rms_size", "gpe_spectrum_nshells", "gpe_spectrum", "gpe_last_error",
-           "gpe_trace_enable", "gpe_trace_count", "gpe_trace_read", "gpe_norm_energy_noalloc"]
+           "gpe_trace_enable", "gpe_trace_count", "gpe_trace_read", "gpe_norm_energy_noalloc",
+           "gpe_batch_create", "gpe_batch_destroy", "gpe_batch_step_real", "gpe_batch_norm_energy",
+           "gpe_batch_groups", "gpe_server_create", "gpe_server_destroy", "gpe_serve_submit", "gpe_serve_poll",
+           "gpe_server_stats"]
 
 
 class GpeError(RuntimeError):
@@ -50,6 +53,30 @@ class gpe_plan_desc(ctypes.Structure):
         ("batch", ctypes.c_int),
         ("g_each", ctypes.POINTER(ctypes.c_double)),
         ("gamma_each", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class gpe_request(ctypes.Structure):
+    _fields_ = [
+        ("desc", gpe_plan_desc),
+        ("imag", ctypes.c_int),
+        ("nsteps", ctypes.c_int64),
+        ("etol", ctypes.c_double),
+        ("check_every", ctypes.c_int),
+        ("target_norm", ctypes.c_double),
+        ("psi0_host", ctypes.c_void_p),
+    ]
+
+
+class gpe_result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("steps_done", ctypes.c_int64),
+        ("norm", ctypes.c_double),
+        ("energy", ctypes.c_double),
+        ("t_submit", ctypes.c_double),
+        ("t_admit", ctypes.c_double),
+        ("t_done", ctypes.c_double),
     ]
 
 
@@ -82,6 +109,17 @@ def lib():
         L.gpe_spectrum.argtypes = [vp, vp, ctypes.c_uint, dp, i64]
         L.gpe_last_error.restype = ctypes.c_char_p
         L.gpe_norm_energy_noalloc.argtypes = [ctypes.POINTER(gpe_plan_desc), vp, vp, dp]
+        L.gpe_batch_create.argtypes = [ctypes.POINTER(gpe_plan_desc), ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.gpe_batch_destroy.argtypes = [vp]
+        L.gpe_batch_step_real.argtypes = [vp, ctypes.POINTER(vp), i64, ctypes.c_int]
+        L.gpe_batch_norm_energy.argtypes = [vp, ctypes.POINTER(vp), dp]
+        L.gpe_batch_groups.argtypes = [vp]
+        L.gpe_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
+        L.gpe_server_destroy.argtypes = [vp]
+        L.gpe_serve_submit.argtypes = [vp, ctypes.POINTER(gpe_request), ctypes.POINTER(ctypes.c_uint64)]
+        L.gpe_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(gpe_result), vp]
+        L.gpe_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_size_t)]
         L.gpe_trace_enable.argtypes = [vp, ctypes.c_int]
         L.gpe_trace_count.argtypes = [vp]
         L.gpe_trace_read.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t,
@@ -287,3 +325,76 @@ class Plan:
             raise TypeError("psi must be a C-contiguous %s array" % np.dtype(want).name)
         gpe_step_real_host(self._h, psi_np.ctypes.data, nsteps)
         return psi_np
+
+
+# ------------------------------------------------------------- batches and serving
+def gpe_batch_create(descs, stream=None):
+    arr = (gpe_plan_desc * len(descs))(*descs)
+    h = ctypes.c_void_p()
+    _check(lib().gpe_batch_create(arr, len(descs), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+    return h
+
+
+def gpe_batch_destroy(batch):
+    _check(lib().gpe_batch_destroy(batch))
+
+
+def _ptr_array(ptrs):
+    return (ctypes.c_void_p * len(ptrs))(*[ctypes.c_void_p(int(p)) for p in ptrs])
+
+
+def gpe_batch_step_real(batch, ptrs, nsteps, use_graph=True):
+    _check(lib().gpe_batch_step_real(batch, _ptr_array(ptrs), int(nsteps), 1 if use_graph else 0))
+
+
+def gpe_batch_norm_energy(batch, ptrs):
+    out = np.zeros(6 * len(ptrs))
+    _check(lib().gpe_batch_norm_energy(batch, _ptr_array(ptrs), _dptr(out)))
+    return out.reshape(len(ptrs), 6)
+
+
+def gpe_batch_groups(batch):
+    return int(lib().gpe_batch_groups(batch))
+
+
+def gpe_server_create(hbm_budget_bytes, max_active, chunk_steps=64):
+    h = ctypes.c_void_p()
+    _check(lib().gpe_server_create(ctypes.c_size_t(int(hbm_budget_bytes)), int(max_active), int(chunk_steps),
+                                   ctypes.byref(h)))
+    return h
+
+
+def gpe_server_destroy(server):
+    _check(lib().gpe_server_destroy(server))
+
+
+def gpe_serve_submit(server, desc, psi0, imag=False, nsteps=1, etol=0.0, check_every=1, target_norm=1.0):
+    """psi0: C-contiguous numpy array (copied by the call)."""
+    r = gpe_request()
+    r.desc = desc
+    r.imag = 1 if imag else 0
+    r.nsteps = int(nsteps)
+    r.etol = float(etol)
+    r.check_every = int(check_every)
+    r.target_norm = float(target_norm)
+    r.psi0_host = psi0.ctypes.data
+    t = ctypes.c_uint64(0)
+    _check(lib().gpe_serve_submit(server, ctypes.byref(r), ctypes.byref(t)))
+    return t.value
+
+
+def gpe_serve_poll(server, ticket, timeout_ms=-1, psi_out=None):
+    """Returns a gpe_result, or None if the request has not finished."""
+    res = gpe_result()
+    rc = lib().gpe_serve_poll(server, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(res),
+                              ctypes.c_void_p(psi_out.ctypes.data if psi_out is not None else 0))
+    if rc == 8:
+        return None
+    _check(rc)
+    return res
+
+
+def gpe_server_stats(server):
+    q, a, u = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_size_t(0)
+    _check(lib().gpe_server_stats(server, ctypes.byref(q), ctypes.byref(a), ctypes.byref(u)))
+    return q.value, a.value, u.value

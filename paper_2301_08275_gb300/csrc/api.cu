@@ -97,6 +97,13 @@ struct gpe_plan {
     int64_t nshells = 0;
     void *host_buf = nullptr;    // device copy for gpe_step_real_host
     std::vector<void *> allocs;
+    // launch context for batches of separately allocated instances (serve.cu):
+    // when cur_count > 0, launches cover cur_count instances found through
+    // cur_ptrs (device array of base pointers) using table slots cur_slots
+    void *const *cur_ptrs = nullptr;
+    const int *cur_slots = nullptr;
+    int64_t cur_count = 0;
+    std::vector<double> gamma_host;   // [batch][3], host copy of the trap parameters
     // tracing
     bool tracing = false;
     struct Rec { std::string kind; cudaEvent_t a, b; };
@@ -120,6 +127,9 @@ struct DeviceGuard {
         if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
 };
+
+// instances covered by the launches of the current call
+static int64_t active_count(const gpe_plan *p) { return p->cur_count > 0 ? p->cur_count : p->batch; }
 
 static int ilog2_64(int64_t v)
 {
@@ -177,6 +187,42 @@ static void destroy(gpe_plan *p)
     for (void *a : p->allocs) cudaFree(a);
     if (p->pin) cudaFreeHost(p->pin);
     delete p;
+}
+
+// Trap tables of one instance on axis a (V_a = gamma^2 x^2 / 2, th = V_a dt):
+// vh = exp(-i th/2) - 1, vf = exp(-i th) - 1 (interleaved re, im), vi = exp(-th/2).
+static void trap_tables_host(const gpe_plan *p, int a, double gamma, double *vh, double *vf, double *vi)
+{
+    const int64_t na = p->n[a];
+    for (int64_t j = 0; j < na; ++j) {
+        const double x = p->lo[a] + (double)j * p->h[a];
+        const double th = 0.5 * gamma * gamma * x * x * p->dt;
+        vh[2 * j] = -2.0 * sin(0.25 * th) * sin(0.25 * th);
+        vh[2 * j + 1] = -sin(0.5 * th);
+        vf[2 * j] = -2.0 * sin(0.5 * th) * sin(0.5 * th);
+        vf[2 * j + 1] = -sin(th);
+        vi[j] = exp(-0.5 * th);
+    }
+}
+
+// complex table values (re, im) in the device format of the plan's precision
+static void pack_cplx(const gpe_plan *p, const std::vector<double> &v, std::vector<unsigned char> &out)
+{
+    if (p->prec != GPE_C64) {
+        out.resize(v.size() * sizeof(double));
+        memcpy(out.data(), v.data(), out.size());
+        return;
+    }
+    std::vector<float> f(v.size() * 2);
+    for (size_t i = 0; i + 1 < v.size(); i += 2) {
+        const float hx = (float)v[i], hy = (float)v[i + 1];
+        f[2 * i + 0] = hx;
+        f[2 * i + 1] = hy;
+        f[2 * i + 2] = (float)(v[i] - (double)hx);
+        f[2 * i + 3] = (float)(v[i + 1] - (double)hy);
+    }
+    out.resize(f.size() * sizeof(float));
+    memcpy(out.data(), f.data(), out.size());
 }
 
 extern "C" gpe_status gpe_plan_create(const gpe_plan_desc *d, void *cuda_stream, gpe_plan **out)
@@ -260,19 +306,8 @@ extern "C" gpe_status gpe_plan_create(const gpe_plan_desc *d, void *cuda_stream,
         PLAN_TRY(upload_real(p, &p->ki[a], ki));
         if (p->trap[a]) {
             std::vector<double> vh(2 * na * B), vf(2 * na * B), vi(na * B);
-            for (int64_t b = 0; b < B; ++b) {
-                const double ga = gam[3 * b + a];
-                for (int64_t j = 0; j < na; ++j) {
-                    const double x = p->lo[a] + (double)j * p->h[a];
-                    const double V = 0.5 * ga * ga * x * x;
-                    const double th = V * p->dt;
-                    vh[2 * (b * na + j)] = -2.0 * sin(0.25 * th) * sin(0.25 * th);
-                    vh[2 * (b * na + j) + 1] = -sin(0.5 * th);
-                    vf[2 * (b * na + j)] = -2.0 * sin(0.5 * th) * sin(0.5 * th);
-                    vf[2 * (b * na + j) + 1] = -sin(th);
-                    vi[b * na + j] = exp(-0.5 * th);
-                }
-            }
+            for (int64_t b = 0; b < B; ++b)
+                trap_tables_host(p, a, gam[3 * b + a], &vh[2 * b * na], &vf[2 * b * na], &vi[b * na]);
             PLAN_TRY(upload_cplx(p, &p->vh[a], vh));
             PLAN_TRY(upload_cplx(p, &p->vf[a], vf));
             PLAN_TRY(upload_real(p, &p->vi[a], vi));
@@ -291,6 +326,7 @@ extern "C" gpe_status gpe_plan_create(const gpe_plan_desc *d, void *cuda_stream,
     PLAN_TRY(dalloc(p, (void **)&p->out4, sizeof(double) * 4 * B));
     PLAN_TRY(dalloc(p, (void **)&p->err, sizeof(int)));
 #undef PLAN_TRY
+    p->gamma_host = gam;
     if (cudaMemcpy(p->g_dev, gs.data(), sizeof(double) * B, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->gamma_dev, gam.data(), sizeof(double) * 3 * B, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess) {
@@ -502,6 +538,11 @@ static PassArgs make_pass(const gpe_plan *p, int axis, const void *src, void *ds
     a.fft1 = a.fft2 = 0;
     a.op_pre = a.op_mid = a.op_post = OP_NONE;
     a.red = RED_NONE;
+    if (p->cur_count > 0 && src == p->cur_ptrs) {
+        a.inst_ptr = p->cur_ptrs;
+        a.slot_of = p->cur_slots;
+        a.src = a.dst = nullptr;
+    }
     return a;
 }
 
@@ -537,7 +578,7 @@ static gpe_status check_psi(const gpe_plan *p, const void *psi)
 static gpe_status step_real_dev(gpe_plan *p, void *psi, int64_t nsteps)
 {
     if (nsteps == 0) return GPE_OK;
-    const int64_t B = p->batch;
+    const int64_t B = active_count(p);
     if (p->ndim == 1) {
         const int64_t chunk = 1 << 16;
         for (int64_t done = 0; done < nsteps; done += chunk) {
@@ -555,6 +596,10 @@ static gpe_status step_real_dev(gpe_plan *p, void *psi, int64_t nsteps)
             l.g = p->g_dev;
             l.dt = p->dt;
             l.err = p->err;
+            if (p->cur_count > 0) {
+                l.inst_ptr = p->cur_ptrs;
+                l.slot_of = p->cur_slots;
+            }
             TraceScope ts(p, "line1d" + std::to_string(l.n) + ":real");
             cudaError_t e = launch_line1d(p->prec, l, p->st);
             if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("1D launch: ") + cudaGetErrorString(e));
@@ -627,7 +672,7 @@ extern "C" gpe_status gpe_step_real_host(gpe_plan *p, void *psi_host, int64_t ns
 // norm/energy/rms of psi into p->out6 / p->out4 (device), enqueued on p->st
 static gpe_status diag_dev(gpe_plan *p, const void *psi)
 {
-    const int64_t B = p->batch;
+    const int64_t B = active_count(p);
     PassArgs x = make_pass(p, 0, psi, nullptr, B);
     x.red = RED_DIAG_X;
     GPE_TRY(run(p, x));
@@ -681,7 +726,7 @@ static gpe_status fill_scale_one(gpe_plan *p)
 
 static gpe_status imag_steps(gpe_plan *p, void *psi, int64_t nsteps, double target)
 {
-    const int64_t B = p->batch;
+    const int64_t B = active_count(p);
     if (nsteps <= 0) return GPE_OK;
     if (p->ndim == 1) {
         Line1DArgs l;
@@ -698,6 +743,10 @@ static gpe_status imag_steps(gpe_plan *p, void *psi, int64_t nsteps, double targ
         l.dt = p->dt;
         l.target_norm_over_dv = target / p->dv;
         l.err = p->err;
+        if (p->cur_count > 0) {
+            l.inst_ptr = p->cur_ptrs;
+            l.slot_of = p->cur_slots;
+        }
         TraceScope ts(p, "line1d" + std::to_string(l.n) + ":imag");
         cudaError_t e = launch_line1d(p->prec, l, p->st);
         if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("1D launch: ") + cudaGetErrorString(e));
@@ -886,3 +935,100 @@ extern "C" gpe_status gpe_spectrum(gpe_plan *p, const void *psi, unsigned kinds,
     }
     return GPE_OK;
 }
+
+// ------------------------------------------------------------------ internal (serve.cu)
+namespace gpe {
+
+cudaStream_t plan_stream(const gpe_plan *p) { return p->st; }
+int64_t plan_capacity(const gpe_plan *p) { return p->batch; }
+int64_t plan_points(const gpe_plan *p) { return p->N; }
+size_t plan_point_bytes(const gpe_plan *p) { return p->csize; }
+
+// Resolve every kernel the plan will launch (function attributes, occupancy)
+// with zero-work launches, so that later launches can be captured in graphs.
+gpe_status plan_prepare(gpe_plan *p)
+{
+    DeviceGuard dg(p->device);
+    for (int a = 0; a < p->ndim; ++a) {
+        PassArgs t = make_pass(p, a, nullptr, nullptr, 0);
+        t.ntiles = 0;
+        cudaError_t e = launch_pass(p->prec, a == 0, t, p->st);
+        if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("prepare: ") + cudaGetErrorString(e));
+    }
+    if (p->ndim == 1) {
+        Line1DArgs l;
+        memset(&l, 0, sizeof(l));
+        l.n = (int)p->n[0];
+        l.batch = 0;
+        cudaError_t e = launch_line1d(p->prec, l, p->st);
+        if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("prepare: ") + cudaGetErrorString(e));
+    }
+    return GPE_OK;
+}
+
+// Give slot `slot` of a plan new interaction and trap parameters: host FP64
+// tables, uploaded on the plan stream.  Axes without a trap table keep none
+// (the caller groups instances by which axes are trapped).
+gpe_status plan_set_slot(gpe_plan *p, int64_t slot, double g, const double *gamma)
+{
+    if (slot < 0 || slot >= p->batch) return fail(GPE_EINVAL, "slot out of range");
+    DeviceGuard dg(p->device);
+    GPE_CUDA(cudaMemcpyAsync(p->g_dev + slot, &g, sizeof(double), cudaMemcpyHostToDevice, p->st));
+    double gm[3] = {0, 0, 0};
+    for (int a = 0; a < p->ndim; ++a) gm[a] = gamma[a];
+    GPE_CUDA(cudaMemcpyAsync(p->gamma_dev + 3 * slot, gm, sizeof(gm), cudaMemcpyHostToDevice, p->st));
+    for (int a = 0; a < p->ndim; ++a) {
+        if (!p->trap[a]) continue;
+        const int64_t na = p->n[a];
+        std::vector<double> vh(2 * na), vf(2 * na), vi(na);
+        trap_tables_host(p, a, gm[a], vh.data(), vf.data(), vi.data());
+        std::vector<unsigned char> bh, bf;
+        pack_cplx(p, vh, bh);
+        pack_cplx(p, vf, bf);
+        const size_t ce = bh.size() / (size_t)na;      // bytes per complex entry
+        GPE_CUDA(cudaMemcpyAsync((char *)p->vh[a] + slot * na * ce, bh.data(), bh.size(), cudaMemcpyHostToDevice, p->st));
+        GPE_CUDA(cudaMemcpyAsync((char *)p->vf[a] + slot * na * ce, bf.data(), bf.size(), cudaMemcpyHostToDevice, p->st));
+        if (p->prec == GPE_C64) {
+            std::vector<float> f(vi.begin(), vi.end());
+            GPE_CUDA(cudaMemcpyAsync((float *)p->vi[a] + slot * na, f.data(), f.size() * sizeof(float),
+                                     cudaMemcpyHostToDevice, p->st));
+            GPE_CUDA(cudaStreamSynchronize(p->st));    // host staging goes out of scope
+        } else {
+            GPE_CUDA(cudaMemcpyAsync((double *)p->vi[a] + slot * na, vi.data(), vi.size() * sizeof(double),
+                                     cudaMemcpyHostToDevice, p->st));
+            GPE_CUDA(cudaStreamSynchronize(p->st));
+        }
+    }
+    GPE_CUDA(cudaStreamSynchronize(p->st));
+    return GPE_OK;
+}
+
+// Run `count` instances found through the device arrays dptrs (base pointers)
+// and dslots (parameter slots): mode 0 = nsteps real-time steps, 1 = nsteps
+// imaginary-time steps renormalised to target, 2 = diagnostics into
+// out6_host[6*count] (norm, E_kin, E_pot, E_int, E, mu).
+gpe_status plan_run(gpe_plan *p, int mode, void *const *dptrs, const int *dslots, int64_t count, int64_t nsteps,
+                    double target, double *out6_host)
+{
+    if (count < 1 || count > p->batch) return fail(GPE_EINVAL, "instance count out of range");
+    DeviceGuard dg(p->device);
+    p->cur_ptrs = dptrs;
+    p->cur_slots = dslots;
+    p->cur_count = count;
+    gpe_status s = GPE_OK;
+    void *psi = const_cast<void *>(static_cast<const void *>(dptrs));
+    if (mode == 0) s = step_real_dev(p, psi, nsteps);
+    else if (mode == 1) {
+        s = imag_steps(p, psi, nsteps, target);
+        if (s == GPE_OK) s = check_err(p);
+    } else {
+        s = diag_dev(p, psi);
+        if (s == GPE_OK) s = copy_out(p, p->out6, 6 * (size_t)count, out6_host);
+    }
+    p->cur_ptrs = nullptr;
+    p->cur_slots = nullptr;
+    p->cur_count = 0;
+    return s;
+}
+
+}  // namespace gpe

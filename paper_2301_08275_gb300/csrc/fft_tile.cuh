@@ -197,19 +197,22 @@ template <int N> struct Radix {
 
 // ---------------------------------------------------------------- tile engine
 // ROWS = true : lines are contiguous rows (x axis); shared layout row-major with
-//               one pad point every 8 points (keeps stride-r writes conflict-free).
+//               the point index XOR-swizzled inside each 128-byte block
+//               (i ^ ((i / P) mod P), P points per 128 bytes), which keeps both
+//               the contiguous reads and the stride-r Stockham writes free of
+//               bank conflicts.
 // ROWS = false: lines are strided (y or z axis); L lines interleaved point by point.
 template <typename R, int N, int L, bool ROWS> struct Tile {
     using C = typename CT<R>::C;
     static constexpr int E = Radix<N>::E;
     static constexpr int TPL = N / E;
     static constexpr int NT = L * TPL;
-    static constexpr int PADN = N + N / 8;
-    static constexpr int SMEM_POINTS = ROWS ? L * PADN : N * L;
+    static constexpr int P = 128 / (int)sizeof(C);      // points per 128-byte block
+    static constexpr int SMEM_POINTS = N * L;
 
     __device__ __forceinline__ static int sidx(int i, int l)
     {
-        if (ROWS) return l * PADN + i + (i >> 3);
+        if (ROWS) return l * N + (i ^ ((i / P) & (P - 1)));
         return i * L + l;
     }
     __device__ __forceinline__ static int line_of(int t) { return ROWS ? t / TPL : t % L; }
@@ -264,6 +267,107 @@ template <typename R, int N, int L, bool ROWS> struct Tile {
         if constexpr (p < Radix<N>::P) {
             pass<DIR, p>(v, sm, tl, l, tw);
             fft<DIR, p + 1>(v, sm, tl, l, tw);
+        }
+    }
+};
+
+// ---------------------------------------------------------------- line groups
+// Strided tile in which each thread carries LPT adjacent lines (LPT = 2 for
+// complex64): the points (i, l0) and (i, l0+1) are adjacent in shared memory,
+// so every exchange moves 16 bytes per access, and one twiddle read serves
+// both lines.  Thread t works on lines l0 = LPT*(t % NP) ... and points
+// tl + TPL*e with tl = t / NP.
+template <typename R, int N, int L, int LPT> struct GTile {
+    using C = typename CT<R>::C;
+    using U = typename UT<R>::U;
+    static constexpr int E = Radix<N>::E;
+    static constexpr int TPL = N / E;
+    static constexpr int NP = L / LPT;
+    static constexpr int NT = NP * TPL;
+    static constexpr int SMEM_POINTS = N * L;
+    static_assert(L % LPT == 0, "lines per tile must be a multiple of lines per thread");
+
+    __device__ __forceinline__ static int sidx(int i, int l) { return i * L + l; }
+
+    __device__ __forceinline__ static void ld(const C *sm, int i, int l0, C (&v)[LPT][E], int e)
+    {
+        if constexpr (LPT == 2 && sizeof(C) == 8) {
+            const float4 q = *reinterpret_cast<const float4 *>(sm + sidx(i, l0));
+            v[0][e] = mk(q.x, q.y);
+            v[1][e] = mk(q.z, q.w);
+        } else {
+#pragma unroll
+            for (int ln = 0; ln < LPT; ++ln) v[ln][e] = sm[sidx(i, l0 + ln)];
+        }
+    }
+    __device__ __forceinline__ static void st(C *sm, int i, int l0, const C *x)
+    {
+        if constexpr (LPT == 2 && sizeof(C) == 8) {
+            *reinterpret_cast<float4 *>(sm + sidx(i, l0)) = make_float4(x[0].x, x[0].y, x[1].x, x[1].y);
+        } else {
+#pragma unroll
+            for (int ln = 0; ln < LPT; ++ln) sm[sidx(i, l0 + ln)] = x[ln];
+        }
+    }
+
+    template <int DIR, int p>
+    __device__ __forceinline__ static void pass(C (&v)[LPT][E], C *sm, int tl, int l0, const U *__restrict__ tw)
+    {
+        constexpr int r = Radix<N>::radix(p);
+        constexpr int Ns = Radix<N>::ns(p);
+        constexpr int B = E / r;
+        constexpr bool last = (p == Radix<N>::P - 1);
+        if constexpr (p > 0) {
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < E; ++e) ld(sm, tl + TPL * e, l0, v, e);
+            if constexpr (!last) __syncthreads();
+        } else if constexpr (!last) {
+            __syncthreads();
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            const int j = tl + q * TPL;
+            const int k = j & (Ns - 1);
+            C x[LPT][r];
+#pragma unroll
+            for (int ln = 0; ln < LPT; ++ln)
+#pragma unroll
+                for (int m = 0; m < r; ++m) x[ln][m] = v[ln][q + m * B];
+            if constexpr (Ns > 1) {
+#pragma unroll
+                for (int m = 1; m < r; ++m) {
+                    const U w = tw[m * k * (N / (Ns * r))];
+#pragma unroll
+                    for (int ln = 0; ln < LPT; ++ln) x[ln][m] = umul<(DIR > 0)>(x[ln][m], w);
+                }
+            }
+#pragma unroll
+            for (int ln = 0; ln < LPT; ++ln) Dft<r, DIR, C>::run(x[ln]);
+            if constexpr (last) {
+#pragma unroll
+                for (int ln = 0; ln < LPT; ++ln)
+#pragma unroll
+                    for (int m = 0; m < r; ++m) v[ln][q + m * B] = x[ln][m];
+            } else {
+                const int base = (j / Ns) * Ns * r + k;
+#pragma unroll
+                for (int m = 0; m < r; ++m) {
+                    C y[LPT];
+#pragma unroll
+                    for (int ln = 0; ln < LPT; ++ln) y[ln] = x[ln][m];
+                    st(sm, base + m * Ns, l0, y);
+                }
+            }
+        }
+    }
+
+    template <int DIR, int p = 0>
+    __device__ __forceinline__ static void fft(C (&v)[LPT][E], C *sm, int tl, int l0, const U *tw)
+    {
+        if constexpr (p < Radix<N>::P) {
+            pass<DIR, p>(v, sm, tl, l0, tw);
+            fft<DIR, p + 1>(v, sm, tl, l0, tw);
         }
     }
 };

@@ -54,6 +54,11 @@ struct PassArgs {
     double nl_c;           // theta = g * nl_c * |psi|^2
     double inv_n;          // 1/N applied with the kinetic substep
     const double *scale;   // per-instance renormalisation factor
+    // optional indirection for batches of separately allocated instances:
+    // instance b lives at inst_ptr[b] (src = dst = that pointer) and takes its
+    // parameters and trap tables from slot slot_of[b] instead of b
+    void *const *inst_ptr;
+    const int *slot_of;
     double *partials;      // [NQ][lines_cap] per-line sums
     int64_t lines_cap;
     // diagnostics geometry
@@ -83,6 +88,8 @@ struct Line1DArgs {
     double dt;
     double target_norm_over_dv;   // imag: target norm / cell volume
     int *err;               // set to 1 if a norm turns non-finite or zero
+    void *const *inst_ptr;  // optional: instance b lives at inst_ptr[b]
+    const int *slot_of;     // optional: parameter/table slot of instance b
 };
 cudaError_t launch_line1d(int prec, const Line1DArgs &a, cudaStream_t st);
 

@@ -19,24 +19,51 @@ __device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sinco
 __device__ __forceinline__ float exp_r(float x) { return expf(x); }
 __device__ __forceinline__ double exp_r(double x) { return exp(x); }
 
-// exp(-i th) - 1 = (-2 sin^2(th/2), -sin th), from the half angle so that the
-// offset keeps full relative precision for small th
-template <typename R> __device__ __forceinline__ typename CT<R>::C phase_offset(R th)
+// exp(-i th) - 1 = (cos th - 1, -sin th).  Double precision: from the half
+// angle, (-2 sin^2(th/2), -sin th).  Single precision, |th| <= 1/2: the
+// Maclaurin series of cos th - 1 and sin th to the th^10 / th^11 terms
+// (truncation below 1e-11 relative), evaluated by Horner's rule in th^2;
+// larger angles fall back to sincosf of the half angle.
+__device__ __forceinline__ double2 phase_offset(double th)
 {
-    R s, c;
-    sincos_r((R)0.5 * th, &s, &c);
-    return mk((R)-2 * s * s, (R)-2 * s * c);
+    double s, c;
+    sincos(0.5 * th, &s, &c);
+    return mk(-2.0 * s * s, -2.0 * s * c);
+}
+__device__ __forceinline__ float2 phase_offset(float th)
+{
+    if (fabsf(th) <= 0.5f) {
+        const float u = th * th;
+        const float cm = u * fmaf(u, fmaf(u, fmaf(u, fmaf(u, -2.75573192e-7f, 2.48015873e-5f), -1.38888889e-3f),
+                                           4.16666667e-2f), -0.5f);
+        const float sn = th * fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, -2.50521084e-8f, 2.75573192e-6f),
+                                                          -1.98412698e-4f), 8.33333333e-3f), -1.66666667e-1f), 1.0f);
+        return mk(cm, -sn);
+    }
+    float s, c;
+    sincosf(0.5f * th, &s, &c);
+    return mk(-2.0f * s * s, -2.0f * s * c);
 }
 
-// lines per tile: tile <= 8192 points (complex64) / 4096 (complex128) and
-// <= 1024 threads; strided tiles take 16 (c64) / 8 (c128) adjacent lines so
-// that every row segment is 128 bytes.
-template <typename R, int N, bool ROWS> constexpr int pick_lines()
+// lines per tile: tiles of at most 4096 (complex64) / 2048 (complex128)
+// points and 8 / 4 adjacent lines, so that every point row of a strided tile
+// is a 64-byte segment and two CTAs of <= 512 threads fit on an SM.
+template <typename R, int N> __host__ __device__ constexpr int pick_lines()
 {
-    constexpr int maxpts = sizeof(R) == 4 ? 8192 : 4096;
-    constexpr int lmax = ROWS ? 16 : (sizeof(R) == 4 ? 16 : 8);
+    constexpr int maxpts = sizeof(R) == 4 ? 4096 : 2048;
+    constexpr int lmax = sizeof(R) == 4 ? 8 : 4;
+    constexpr int lmin = 1;
     int L = maxpts / N;
     if (L > lmax) L = lmax;
+    if (L < lmin) L = lmin;
+    return L;
+}
+// the on-chip 1D kernel keeps whole lines per thread group (row layout)
+template <typename R, int N> __host__ __device__ constexpr int pick_lines_1d()
+{
+    constexpr int maxpts = sizeof(R) == 4 ? 8192 : 4096;
+    int L = maxpts / N;
+    if (L > 16) L = 16;
     if (L < 1) L = 1;
     return L;
 }
@@ -59,9 +86,11 @@ __device__ __forceinline__ double line_sum(double x, double *red, int l, int tl)
 }
 
 // pointwise substep on the E points (indices tl + TPL*e on this axis) of one line
+// inst: position of the instance in this launch (renormalisation factor);
+// ti: its parameter/table slot
 template <typename R, int E, int TPL>
 __device__ __forceinline__ void point_op(int op, typename CT<R>::C (&v)[E], const PassArgs &a, int inst,
-                                         int c0, int c1, int tl)
+                                         int ti, int c0, int c1, int tl)
 {
     using C = typename CT<R>::C;
     if (op == OP_NONE) return;
@@ -97,18 +126,18 @@ __device__ __forceinline__ void point_op(int op, typename CT<R>::C (&v)[E], cons
         for (int e = 0; e < E; ++e) v[e] = cscale(v[e], s);
         if (op == OP_SCALE) return;
     }
-    const R gc = (R)(a.g[inst] * a.nl_c);
+    const R gc = (R)(a.g[ti] * a.nl_c);
     if (op == OP_NREAL) {
         // trap tables hold exp(-i V_a c) - 1
         const U *vax = static_cast<const U *>(a.vt_ax);
         const U *v0 = static_cast<const U *>(a.vt_o0);
         const U *v1 = static_cast<const U *>(a.vt_o1);
-        const U f0 = v0 ? v0[(int64_t)inst * a.o0n + c0] : U{};
-        const U f1 = v1 ? v1[(int64_t)inst * a.o1n + c1] : U{};
+        const U f0 = v0 ? v0[(int64_t)ti * a.o0n + c0] : U{};
+        const U f1 = v1 ? v1[(int64_t)ti * a.o1n + c1] : U{};
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             C x = cmadd1(v[e], phase_offset(gc * cabs2(v[e])));
-            if (vax) x = uomul(x, vax[(int64_t)inst * a.nax + tl + TPL * e]);
+            if (vax) x = uomul(x, vax[(int64_t)ti * a.nax + tl + TPL * e]);
             if (v0) x = uomul(x, f0);
             if (v1) x = uomul(x, f1);
             v[e] = x;
@@ -118,118 +147,254 @@ __device__ __forceinline__ void point_op(int op, typename CT<R>::C (&v)[E], cons
     // OP_NIMAG / OP_SCALE_NIMAG
     const R *iax = static_cast<const R *>(a.vi_ax);
     R fl = (R)1;
-    if (a.vi_o0) fl *= static_cast<const R *>(a.vi_o0)[(int64_t)inst * a.o0n + c0];
-    if (a.vi_o1) fl *= static_cast<const R *>(a.vi_o1)[(int64_t)inst * a.o1n + c1];
+    if (a.vi_o0) fl *= static_cast<const R *>(a.vi_o0)[(int64_t)ti * a.o0n + c0];
+    if (a.vi_o1) fl *= static_cast<const R *>(a.vi_o1)[(int64_t)ti * a.o1n + c1];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         R f = fl * exp_r(-gc * cabs2(v[e]));
-        if (iax) f *= iax[(int64_t)inst * a.nax + tl + TPL * e];
+        if (iax) f *= iax[(int64_t)ti * a.nax + tl + TPL * e];
         v[e] = cscale(v[e], f);
     }
 }
 
-template <typename R, int N, int L, bool ROWS>
-__global__ void __launch_bounds__(Tile<R, N, L, ROWS>::NT) k_pass(const PassArgs a)
+// asynchronous global -> shared copies of one point (cp.async, no register staging)
+__device__ __forceinline__ void cp_async_point(void *smem, const float2 *g)
 {
-    using T = Tile<R, N, L, ROWS>;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(g));
+}
+__device__ __forceinline__ void cp_async_point(void *smem, const double2 *g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(g));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int K> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K)); }
+
+// Geometry of the line a thread works on in a given tile.
+struct LineGeom {
+    int64_t lg, li, off;   // off: offset of the line start from the instance base
+    int inst, ti, c0, c1;
+    bool valid;
+};
+template <int L>
+__device__ __forceinline__ LineGeom line_geom(const PassArgs &a, int64_t tile, int l)
+{
+    LineGeom g;
+    g.lg = tile * L + l;
+    g.valid = g.lg < a.lines_total;
+    g.inst = g.valid ? int(g.lg >> a.lg_lpi) : 0;
+    g.ti = a.slot_of ? a.slot_of[g.inst] : g.inst;
+    g.li = g.lg & ((int64_t(1) << a.lg_lpi) - 1);
+    g.c0 = int(g.li & (a.o0n - 1));
+    g.c1 = int(g.li >> a.lg_o0);
+    g.off = (g.li & ((int64_t(1) << a.lg_A) - 1)) + (g.li >> a.lg_A) * a.Sb;
+    return g;
+}
+// base pointers of an instance (inst_ptr indirection or back-to-back storage)
+template <typename C>
+__device__ __forceinline__ const C *inst_src(const PassArgs &a, int inst)
+{
+    return a.inst_ptr ? static_cast<const C *>(a.inst_ptr[inst]) : static_cast<const C *>(a.src) + inst * a.inst_stride;
+}
+template <typename C> __device__ __forceinline__ C *inst_dst(const PassArgs &a, int inst)
+{
+    return a.inst_ptr ? static_cast<C *>(a.inst_ptr[inst]) : static_cast<C *>(a.dst) + inst * a.inst_stride;
+}
+
+// Per-line sums for the LPT lines of every thread: each line's TPL partial
+// values are added in a fixed tree order; all threads of the group receive
+// the totals.
+template <int L, int TPL, int LPT>
+__device__ __forceinline__ void group_sum(double (&x)[LPT], double *red, int l0, int tl)
+{
+#pragma unroll
+    for (int ln = 0; ln < LPT; ++ln) red[tl * L + l0 + ln] = x[ln];
+    __syncthreads();
+#pragma unroll 1
+    for (int s = TPL / 2; s > 0; s >>= 1) {
+        if (tl < s) {
+#pragma unroll
+            for (int ln = 0; ln < LPT; ++ln) red[tl * L + l0 + ln] += red[(tl + s) * L + l0 + ln];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int ln = 0; ln < LPT; ++ln) x[ln] = red[l0 + ln];
+    __syncthreads();
+}
+
+// lines carried by each thread.  Two lines per thread (16-byte shared accesses,
+// one twiddle read for both) measured slower on the strided axes at 512^3
+// (occupancy halves at 122 registers), so each thread carries one line.
+template <typename R> __host__ __device__ constexpr int lines_per_thread() { return 1; }
+
+// One sweep over every line of one axis.  Threads are laid out across the
+// lines of a tile (a thread carries LPT adjacent lines at points t / NP +
+// TPL*e), so that warp-wide accesses to consecutive lines are contiguous for
+// the y and z axes and every twiddle read in a Stockham pass is a broadcast
+// shared by the thread's lines.  Tiles are software-pipelined: the points of
+// tile i+2 are copied into one of two shared buffers with cp.async while tile
+// i is transformed in the other.
+template <typename R, int N, int L>
+__global__ void __launch_bounds__(GTile<R, N, L, lines_per_thread<R>()>::NT, 2) k_pass(const PassArgs a)
+{
+    constexpr int LPT = lines_per_thread<R>();
+    using T = GTile<R, N, L, LPT>;
     using C = typename T::C;
+    using U = typename T::U;
     constexpr int E = T::E, TPL = T::TPL;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C *sm = reinterpret_cast<C *>(smraw);
-    double *red = reinterpret_cast<double *>(smraw + sizeof(C) * T::SMEM_POINTS);
-    const int t = threadIdx.x, l = T::line_of(t), tl = T::tl_of(t);
-    const typename T::U *tw = static_cast<const typename T::U *>(a.tw);
-    const C *src = static_cast<const C *>(a.src);
-    C *dst = static_cast<C *>(a.dst);
-    const int64_t lpi_mask = (int64_t(1) << a.lg_lpi) - 1;
-    const int64_t a_mask = (int64_t(1) << a.lg_A) - 1;
+    C *buf0 = reinterpret_cast<C *>(smraw);
+    C *buf1 = buf0 + T::SMEM_POINTS;
+    double *red = reinterpret_cast<double *>(smraw + 2 * sizeof(C) * T::SMEM_POINTS);
+    U *tw = reinterpret_cast<U *>(smraw + 2 * sizeof(C) * T::SMEM_POINTS + sizeof(double) * N * L / E);
+    const int t = threadIdx.x, l0 = (t % T::NP) * LPT, tl = t / T::NP;
+    for (int i = t; i < N; i += T::NT) tw[i] = static_cast<const U *>(a.tw)[i];
 
-    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        const int64_t lg = tile * L + l;
-        const bool valid = lg < a.lines_total;
-        const int inst = valid ? int(lg >> a.lg_lpi) : 0;
-        const int64_t li = lg & lpi_mask;
-        const int c0 = int(li & (a.o0n - 1)), c1 = int(li >> a.lg_o0);
-        const int64_t base = inst * a.inst_stride + (li & a_mask) + (li >> a.lg_A) * a.Sb;
-        C v[E];
+    auto stage = [&](int64_t tile, C *buf) {
+        if (tile < a.ntiles) {
 #pragma unroll
-        for (int e = 0; e < E; ++e)
-            v[e] = valid ? src[base + (int64_t)(tl + TPL * e) * a.estride] : mk((R)0, (R)0);
+            for (int ln = 0; ln < LPT; ++ln) {
+                const LineGeom g = line_geom<L>(a, tile, l0 + ln);
+                if (g.valid) {
+                    const C *src = inst_src<C>(a, g.inst) + g.off;
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        cp_async_point(buf + T::sidx(tl + TPL * e, l0 + ln), src + (int64_t)(tl + TPL * e) * a.estride);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+
+    int64_t tile = blockIdx.x;
+    stage(tile, buf0);
+    stage(tile + gridDim.x, buf1);
+    for (int it = 0; tile < a.ntiles; ++it, tile += gridDim.x) {
+        C *sm = (it & 1) ? buf1 : buf0;
+        cp_async_wait<1>();      // this tile's copies are done (the next tile's may still fly)
+        __syncthreads();
+        LineGeom g[LPT];
+#pragma unroll
+        for (int ln = 0; ln < LPT; ++ln) g[ln] = line_geom<L>(a, tile, l0 + ln);
+        C v[LPT][E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) T::ld(sm, tl + TPL * e, l0, v, e);
+#pragma unroll
+        for (int ln = 0; ln < LPT; ++ln)
+            if (!g[ln].valid)
+#pragma unroll
+                for (int e = 0; e < E; ++e) v[ln][e] = mk((R)0, (R)0);
 
         if (a.red == RED_DIAG_X) {
-            // real-space moments of rho = |psi|^2 along the row, then kx^2 |F_x psi|^2
-            const double gx = a.gamma[3 * inst + 0];
+            // real-space moments of rho = |psi|^2 along each row, then kx^2 |F_x psi|^2
             const R lox = (R)a.lo[0], hx = (R)a.h[0];
-            R s0 = 0, sx2 = 0, s4 = 0;
+            R s0[LPT], sx2[LPT], s4[LPT];
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const R x = lox + (R)(tl + TPL * e) * hx;
-                const R rho = cabs2(v[e]);
-                s0 += rho;
-                sx2 += x * x * rho;
-                s4 += rho * rho;
+            for (int ln = 0; ln < LPT; ++ln) {
+                s0[ln] = sx2[ln] = s4[ln] = (R)0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const R x = lox + (R)(tl + TPL * e) * hx;
+                    const R rho = cabs2(v[ln][e]);
+                    s0[ln] += rho;
+                    sx2[ln] += x * x * rho;
+                    s4[ln] += rho * rho;
+                }
             }
-            T::template fft<-1>(v, sm, tl, l, tw);
+            T::template fft<-1>(v, sm, tl, l0, tw);
             const R kf = (R)a.kf[0];
-            R sk = 0;
+            R sk[LPT];
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int i = tl + TPL * e;
-                const R k = kf * (R)(i < N / 2 ? i : i - N);
-                sk += k * k * cabs2(v[e]);
+            for (int ln = 0; ln < LPT; ++ln) {
+                sk[ln] = (R)0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int i = tl + TPL * e;
+                    const R k = kf * (R)(i < N / 2 ? i : i - N);
+                    sk[ln] += k * k * cabs2(v[ln][e]);
+                }
             }
-            const double y = a.lo[1] + (double)c0 * a.h[1], z = a.lo[2] + (double)c1 * a.h[2];
-            const double gy = a.gamma[3 * inst + 1], gz = a.gamma[3 * inst + 2];
-            const double vyz = 0.5 * gy * gy * y * y + 0.5 * gz * gz * z * z;
-            double q[7];
-            q[0] = (double)s0;
-            q[1] = (double)sx2;
-            q[2] = y * y * (double)s0;
-            q[3] = z * z * (double)s0;
-            q[4] = 0.5 * gx * gx * (double)sx2 + vyz * (double)s0;
-            q[5] = (double)s4;
-            q[6] = (double)sk;
+            double q[7][LPT];
+#pragma unroll
+            for (int ln = 0; ln < LPT; ++ln) {
+                const int ti = g[ln].ti;
+                const double y = a.lo[1] + (double)g[ln].c0 * a.h[1], z = a.lo[2] + (double)g[ln].c1 * a.h[2];
+                const double gx = a.gamma[3 * ti + 0], gy = a.gamma[3 * ti + 1], gz = a.gamma[3 * ti + 2];
+                const double vyz = 0.5 * gy * gy * y * y + 0.5 * gz * gz * z * z;
+                q[0][ln] = (double)s0[ln];
+                q[1][ln] = (double)sx2[ln];
+                q[2][ln] = y * y * (double)s0[ln];
+                q[3][ln] = z * z * (double)s0[ln];
+                q[4][ln] = 0.5 * gx * gx * (double)sx2[ln] + vyz * (double)s0[ln];
+                q[5][ln] = (double)s4[ln];
+                q[6][ln] = (double)sk[ln];
+            }
 #pragma unroll 1
             for (int k = 0; k < 7; ++k) {
-                const double s = line_sum<L, TPL>(q[k], red, l, tl);
-                if (tl == 0 && valid) a.partials[(int64_t)k * a.lines_cap + lg] = s;
+                group_sum<L, TPL, LPT>(q[k], red, l0, tl);
+#pragma unroll
+                for (int ln = 0; ln < LPT; ++ln)
+                    if (tl == 0 && g[ln].valid) a.partials[(int64_t)k * a.lines_cap + g[ln].lg] = q[k][ln];
             }
-            continue;
-        }
-        if (a.red == RED_DIAG_K) {
-            T::template fft<-1>(v, sm, tl, l, tw);
+        } else if (a.red == RED_DIAG_K) {
+            T::template fft<-1>(v, sm, tl, l0, tw);
             const R kf = (R)a.kf[a.axis];
-            R sk = 0;
+            double sk[LPT];
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int i = tl + TPL * e;
-                const R k = kf * (R)(i < N / 2 ? i : i - N);
-                sk += k * k * cabs2(v[e]);
+            for (int ln = 0; ln < LPT; ++ln) {
+                R acc = (R)0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int i = tl + TPL * e;
+                    const R k = kf * (R)(i < N / 2 ? i : i - N);
+                    acc += k * k * cabs2(v[ln][e]);
+                }
+                sk[ln] = (double)acc;
             }
-            const double s = line_sum<L, TPL>((double)sk, red, l, tl);
-            if (tl == 0 && valid) a.partials[(int64_t)(6 + a.axis) * a.lines_cap + lg] = s;
-            continue;
-        }
-
-        point_op<R, E, TPL>(a.op_pre, v, a, inst, c0, c1, tl);
-        if (a.fft1 < 0) T::template fft<-1>(v, sm, tl, l, tw);
-        else if (a.fft1 > 0) T::template fft<1>(v, sm, tl, l, tw);
-        point_op<R, E, TPL>(a.op_mid, v, a, inst, c0, c1, tl);
-        if (a.fft2 < 0) T::template fft<-1>(v, sm, tl, l, tw);
-        else if (a.fft2 > 0) T::template fft<1>(v, sm, tl, l, tw);
-        point_op<R, E, TPL>(a.op_post, v, a, inst, c0, c1, tl);
-        if (a.red == RED_NORM) {
-            double s = 0.0;
+            group_sum<L, TPL, LPT>(sk, red, l0, tl);
 #pragma unroll
-            for (int e = 0; e < E; ++e) s += (double)cabs2(v[e]);
-            s = line_sum<L, TPL>(s, red, l, tl);
-            if (tl == 0 && valid) a.partials[lg] = s;
-        }
-        if (valid) {
+            for (int ln = 0; ln < LPT; ++ln)
+                if (tl == 0 && g[ln].valid) a.partials[(int64_t)(6 + a.axis) * a.lines_cap + g[ln].lg] = sk[ln];
+        } else {
 #pragma unroll
-            for (int e = 0; e < E; ++e) dst[base + (int64_t)(tl + TPL * e) * a.estride] = v[e];
+            for (int ln = 0; ln < LPT; ++ln)
+                point_op<R, E, TPL>(a.op_pre, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl);
+            if (a.fft1 < 0) T::template fft<-1>(v, sm, tl, l0, tw);
+            else if (a.fft1 > 0) T::template fft<1>(v, sm, tl, l0, tw);
+#pragma unroll
+            for (int ln = 0; ln < LPT; ++ln)
+                point_op<R, E, TPL>(a.op_mid, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl);
+            if (a.fft2 < 0) T::template fft<-1>(v, sm, tl, l0, tw);
+            else if (a.fft2 > 0) T::template fft<1>(v, sm, tl, l0, tw);
+#pragma unroll
+            for (int ln = 0; ln < LPT; ++ln)
+                point_op<R, E, TPL>(a.op_post, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl);
+            if (a.red == RED_NORM) {
+                double sn[LPT];
+#pragma unroll
+                for (int ln = 0; ln < LPT; ++ln) {
+                    sn[ln] = 0.0;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) sn[ln] += (double)cabs2(v[ln][e]);
+                }
+                group_sum<L, TPL, LPT>(sn, red, l0, tl);
+#pragma unroll
+                for (int ln = 0; ln < LPT; ++ln)
+                    if (tl == 0 && g[ln].valid) a.partials[g[ln].lg] = sn[ln];
+            }
+#pragma unroll
+            for (int ln = 0; ln < LPT; ++ln) {
+                if (g[ln].valid) {
+                    C *dst = inst_dst<C>(a, g[ln].inst) + g[ln].off;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) dst[(int64_t)(tl + TPL * e) * a.estride] = v[ln][e];
+                }
+            }
         }
+        __syncthreads();         // every thread is done with this buffer
+        stage(tile + 2 * (int64_t)gridDim.x, sm);
     }
+    cp_async_wait<0>();
 }
 
 // ------------------------------------------------------------------ 1D on chip
@@ -242,22 +407,26 @@ __global__ void __launch_bounds__(Tile<R, N, L, true>::NT) k_line1d(const Line1D
     using T = Tile<R, N, L, true>;
     using C = typename T::C;
     constexpr int E = T::E, TPL = T::TPL;
+    using U = typename T::U;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
     double *red = reinterpret_cast<double *>(smraw + sizeof(C) * T::SMEM_POINTS);
+    U *tw = reinterpret_cast<U *>(smraw + sizeof(C) * T::SMEM_POINTS + sizeof(double) * T::NT);
     const int t = threadIdx.x, l = T::line_of(t), tl = T::tl_of(t);
-    using U = typename T::U;
-    const U *tw = static_cast<const U *>(a.tw);
-    C *psi = static_cast<C *>(a.psi);
+    for (int i = t; i < N; i += T::NT) tw[i] = static_cast<const U *>(a.tw)[i];
+    __syncthreads();
     const int64_t ntiles = (a.batch + L - 1) / L;
 
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t inst = tile * L + l;
         const bool valid = inst < a.batch;
-        const int64_t ib = valid ? inst : 0;
+        const int64_t ip = valid ? inst : 0;
+        // instance storage and its parameter/table slot
+        C *psi = a.inst_ptr ? static_cast<C *>(a.inst_ptr[ip]) : static_cast<C *>(a.psi) + ip * N;
+        const int64_t ib = a.slot_of ? a.slot_of[ip] : ip;
         C v[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = valid ? psi[ib * N + tl + TPL * e] : mk((R)0, (R)0);
+        for (int e = 0; e < E; ++e) v[e] = valid ? psi[tl + TPL * e] : mk((R)0, (R)0);
         const double g = a.g[ib];
         if (!a.imag) {
             const U *kt = static_cast<const U *>(a.kt);
@@ -325,7 +494,7 @@ __global__ void __launch_bounds__(Tile<R, N, L, true>::NT) k_line1d(const Line1D
         }
         if (valid) {
 #pragma unroll
-            for (int e = 0; e < E; ++e) psi[ib * N + tl + TPL * e] = v[e];
+            for (int e = 0; e < E; ++e) psi[tl + TPL * e] = v[e];
         }
     }
 }
@@ -359,27 +528,28 @@ static cudaError_t prepare(K kern, LaunchCache &lc, int nt, size_t smem, int *ca
     return cudaSuccess;
 }
 
-template <typename R, int N, bool ROWS> static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st)
+template <typename R, int N> static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st)
 {
-    constexpr int L = pick_lines<R, N, ROWS>();
-    using T = Tile<R, N, L, ROWS>;
+    constexpr int L = pick_lines<R, N>();
+    using T = GTile<R, N, L, lines_per_thread<R>()>;
     static LaunchCache lc;
-    const size_t smem = sizeof(typename T::C) * T::SMEM_POINTS + sizeof(double) * T::NT;
+    const size_t smem = 2 * sizeof(typename T::C) * T::SMEM_POINTS + sizeof(double) * (N * L / T::E) +
+                        sizeof(typename T::U) * N;
     int cap = 0;
-    cudaError_t e = prepare(k_pass<R, N, L, ROWS>, lc, T::NT, smem, &cap);
+    cudaError_t e = prepare(k_pass<R, N, L>, lc, T::NT, smem, &cap);
     if (e != cudaSuccess) return e;
     if (a.ntiles <= 0) return cudaSuccess;
     const int grid = (int)(a.ntiles < cap ? a.ntiles : cap);
-    k_pass<R, N, L, ROWS><<<grid, T::NT, smem, st>>>(a);
+    k_pass<R, N, L><<<grid, T::NT, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename R, int N> static cudaError_t launch_line1d_t(const Line1DArgs &a, cudaStream_t st)
 {
-    constexpr int L = pick_lines<R, N, true>();
+    constexpr int L = pick_lines_1d<R, N>();
     using T = Tile<R, N, L, true>;
     static LaunchCache lc;
-    const size_t smem = sizeof(typename T::C) * T::SMEM_POINTS + sizeof(double) * T::NT;
+    const size_t smem = sizeof(typename T::C) * T::SMEM_POINTS + sizeof(double) * T::NT + sizeof(typename T::U) * N;
     int cap = 0;
     cudaError_t e = prepare(k_line1d<R, N, L>, lc, T::NT, smem, &cap);
     if (e != cudaSuccess) return e;
@@ -392,22 +562,22 @@ template <typename R, int N> static cudaError_t launch_line1d_t(const Line1DArgs
 
 #define GPE_FOR_EACH_N(X) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
 
-template <typename R> static cudaError_t launch_pass_r(bool rows, const PassArgs &a, cudaStream_t st)
+template <typename R> static cudaError_t launch_pass_r(bool, const PassArgs &a, cudaStream_t st)
 {
     switch (a.nax) {
 #define GPE_CASE(NN) \
-    case NN: return rows ? launch_pass_t<R, NN, true>(a, st) : launch_pass_t<R, NN, false>(a, st);
+    case NN: return launch_pass_t<R, NN>(a, st);
         GPE_FOR_EACH_N(GPE_CASE)
 #undef GPE_CASE
     default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename R> static int lines_per_tile_r(bool rows, int n)
+template <typename R> static int lines_per_tile_r(bool, int n)
 {
     switch (n) {
 #define GPE_CASE(NN) \
-    case NN: return rows ? pick_lines<R, NN, true>() : pick_lines<R, NN, false>();
+    case NN: return pick_lines<R, NN>();
         GPE_FOR_EACH_N(GPE_CASE)
 #undef GPE_CASE
     default: return 0;

@@ -1,0 +1,73 @@
+"""Host-side logic that needs no GPU: ABI struct layouts of the serving API and
+the multi-rank timing aggregation of bench.py (gloo, world size 2)."""
+import ctypes
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _offsets_from_c(struct, fields):
+    src = '#include <stdio.h>\n#include <stddef.h>\n#include "gpe_serve.h"\nint main(void){printf("%zu' + \
+        ' %zu' * len(fields) + '\\n", sizeof(%s)' % struct + ''.join(', offsetof(%s, %s)' % (struct, f) for f in fields) + \
+        ');return 0;}\n'
+    d = "/tmp/gpe_layout_%d_%s" % (os.getpid(), struct)
+    os.makedirs(d, exist_ok=True)
+    open(os.path.join(d, "c.c"), "w").write(src)
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), os.path.join(d, "c.c"), "-o", os.path.join(d, "c")],
+                   check=True)
+    return [int(v) for v in subprocess.run([os.path.join(d, "c")], capture_output=True, text=True,
+                                           check=True).stdout.split()]
+
+
+@pytest.mark.parametrize("name", ["gpe_request", "gpe_result"])
+def test_serving_structs_match_header(name):
+    import paper_2301_08275_gb300 as gpe
+    S = getattr(gpe, name)
+    fields = [f for f, _ in S._fields_]
+    assert _offsets_from_c(name, fields) == [ctypes.sizeof(S)] + [getattr(S, f).offset for f in fields]
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        q.put((rank, bench.max_over_ranks(10.0 + 5.0 * rank)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_world2():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    for p in ps:
+        p.join(120)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(2))
+    assert got == {0: 15.0, 1: 15.0}
+
+
+def test_max_over_ranks_single_process():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5) == 3.5
