@@ -272,12 +272,18 @@ template <typename R, int N, int L, bool ROWS> struct Tile {
 };
 
 // ---------------------------------------------------------------- line groups
-// Strided tile in which each thread carries LPT adjacent lines (LPT = 2 for
-// complex64): the points (i, l0) and (i, l0+1) are adjacent in shared memory,
-// so every exchange moves 16 bytes per access, and one twiddle read serves
-// both lines.  Thread t works on lines l0 = LPT*(t % NP) ... and points
-// tl + TPL*e with tl = t / NP.
-template <typename R, int N, int L, int LPT> struct GTile {
+// Strided tile in which each thread carries LPT adjacent lines: the points
+// (i, l0) ... (i, l0+LPT-1) are adjacent in shared memory and one twiddle read
+// serves all of them.  Thread t works on lines l0 = LPT*(t % NP) ... and
+// points tl + TPL*e with tl = t / NP.
+//
+// SW = true XOR-swizzles the point index: the low bits of i are flipped by the
+// bits just above the first radix, so that the stride-r writes of the first
+// Stockham pass (lanes with consecutive tl write points r apart) fall into
+// distinct 128-byte bank rows when a point row (L points) is narrower than a
+// bank row.  The map is a bijection of [0, N): every flipped bit is flipped by
+// a higher bit, which it does not change.
+template <typename R, int N, int L, int LPT, bool SW = false> struct GTile {
     using C = typename CT<R>::C;
     using U = typename UT<R>::U;
     static constexpr int E = Radix<N>::E;
@@ -287,7 +293,13 @@ template <typename R, int N, int L, int LPT> struct GTile {
     static constexpr int SMEM_POINTS = N * L;
     static_assert(L % LPT == 0, "lines per tile must be a multiple of lines per thread");
 
-    __device__ __forceinline__ static int sidx(int i, int l) { return i * L + l; }
+    static constexpr int QS = 128 / (L * (int)sizeof(C)) > 1 ? 128 / (L * (int)sizeof(C)) : 1;
+    static constexpr int SWS = ilog2c(Radix<N>::radix(0));
+    __device__ __forceinline__ static int sidx(int i, int l)
+    {
+        if constexpr (SW) return (i ^ ((i >> SWS) & (QS - 1))) * L + l;
+        return i * L + l;
+    }
 
     __device__ __forceinline__ static void ld(const C *sm, int i, int l0, C (&v)[LPT][E], int e)
     {

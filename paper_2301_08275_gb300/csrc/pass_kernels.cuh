@@ -45,13 +45,26 @@ __device__ __forceinline__ float2 phase_offset(float th)
     return mk(-2.0f * s * s, -2.0f * s * c);
 }
 
-// lines per tile: tiles of at most 4096 (complex64) / 2048 (complex128)
-// points and 8 / 4 adjacent lines, so that every point row of a strided tile
-// is a 64-byte segment and two CTAs of <= 512 threads fit on an SM.
-template <typename R, int N> __host__ __device__ constexpr int pick_lines()
+// lines per tile.  Strided lines (y, z) of complex64: tiles of at most 8192
+// points and 16 adjacent lines, so that every point row of a tile is a
+// 128-byte segment (one CTA of <= 1024 threads per SM); with 8 lines (64-byte
+// pieces) the z sweep of a 512^3 grid, whose consecutive points are 2 MiB
+// apart, ran at under half the copy bandwidth.  Complex128: 2048 points and
+// 4 lines (64-byte pieces), two CTAs per SM.
+// Contiguous rows (x) of complex64 with N <= 512 use tiles of 4 rows at four
+// CTAs per SM and the swizzled shared layout: there each lane's points lie in
+// its own row, and fewer rows per warp request with longer pieces of each
+// (4 rows x 64 bytes rather than 8 x 32) measured faster.  Longer rows and
+// complex128 rows take the strided choice.
+template <typename R, int N, bool ROWS> __host__ __device__ constexpr bool rows_split()
 {
-    constexpr int maxpts = sizeof(R) == 4 ? 4096 : 2048;
-    constexpr int lmax = sizeof(R) == 4 ? 8 : 4;
+    return ROWS && sizeof(R) == 4 && N >= 8 && N <= 512;
+}
+template <typename R, int N, bool ROWS> __host__ __device__ constexpr int pick_lines()
+{
+    constexpr bool wide = !ROWS && sizeof(R) == 4;
+    constexpr int maxpts = sizeof(R) == 4 ? (wide ? 8192 : 4096) : 2048;
+    constexpr int lmax = rows_split<R, N, ROWS>() ? 4 : (sizeof(R) == 4 ? (wide ? 16 : 8) : 4);
     constexpr int lmin = 1;
     int L = maxpts / N;
     if (L > lmax) L = lmax;
@@ -234,11 +247,20 @@ template <typename R> __host__ __device__ constexpr int lines_per_thread() { ret
 // shared by the thread's lines.  Tiles are software-pipelined: the points of
 // tile i+2 are copied into one of two shared buffers with cp.async while tile
 // i is transformed in the other.
-template <typename R, int N, int L>
-__global__ void __launch_bounds__(GTile<R, N, L, lines_per_thread<R>()>::NT, 2) k_pass(const PassArgs a)
+template <typename R, int N, int L, bool ROWS> constexpr int pass_min_blocks()
+{
+    constexpr int nt = GTile<R, N, L, lines_per_thread<R>(), rows_split<R, N, ROWS>()>::NT;
+    constexpr int want = 1024 / nt > 16 ? 16 : 1024 / nt;
+    return rows_split<R, N, ROWS>() && want > 2 ? want : (nt > 512 ? 1 : 2);
+}
+
+template <typename R, int N, int L, bool ROWS>
+__global__ void __launch_bounds__(GTile<R, N, L, lines_per_thread<R>(), rows_split<R, N, ROWS>()>::NT,
+                                  (pass_min_blocks<R, N, L, ROWS>()))
+    k_pass(const PassArgs a)
 {
     constexpr int LPT = lines_per_thread<R>();
-    using T = GTile<R, N, L, LPT>;
+    using T = GTile<R, N, L, LPT, rows_split<R, N, ROWS>()>;
     using C = typename T::C;
     using U = typename T::U;
     constexpr int E = T::E, TPL = T::TPL;
@@ -528,19 +550,19 @@ static cudaError_t prepare(K kern, LaunchCache &lc, int nt, size_t smem, int *ca
     return cudaSuccess;
 }
 
-template <typename R, int N> static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st)
+template <typename R, int N, bool ROWS> static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st)
 {
-    constexpr int L = pick_lines<R, N>();
-    using T = GTile<R, N, L, lines_per_thread<R>()>;
+    constexpr int L = pick_lines<R, N, ROWS>();
+    using T = GTile<R, N, L, lines_per_thread<R>(), rows_split<R, N, ROWS>()>;
     static LaunchCache lc;
     const size_t smem = 2 * sizeof(typename T::C) * T::SMEM_POINTS + sizeof(double) * (N * L / T::E) +
                         sizeof(typename T::U) * N;
     int cap = 0;
-    cudaError_t e = prepare(k_pass<R, N, L>, lc, T::NT, smem, &cap);
+    cudaError_t e = prepare(k_pass<R, N, L, ROWS>, lc, T::NT, smem, &cap);
     if (e != cudaSuccess) return e;
     if (a.ntiles <= 0) return cudaSuccess;
     const int grid = (int)(a.ntiles < cap ? a.ntiles : cap);
-    k_pass<R, N, L><<<grid, T::NT, smem, st>>>(a);
+    k_pass<R, N, L, ROWS><<<grid, T::NT, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -562,22 +584,22 @@ template <typename R, int N> static cudaError_t launch_line1d_t(const Line1DArgs
 
 #define GPE_FOR_EACH_N(X) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
 
-template <typename R> static cudaError_t launch_pass_r(bool, const PassArgs &a, cudaStream_t st)
+template <typename R, bool ROWS> static cudaError_t launch_pass_r(const PassArgs &a, cudaStream_t st)
 {
     switch (a.nax) {
 #define GPE_CASE(NN) \
-    case NN: return launch_pass_t<R, NN>(a, st);
+    case NN: return launch_pass_t<R, NN, ROWS>(a, st);
         GPE_FOR_EACH_N(GPE_CASE)
 #undef GPE_CASE
     default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename R> static int lines_per_tile_r(bool, int n)
+template <typename R> static int lines_per_tile_r(bool rows, int n)
 {
     switch (n) {
 #define GPE_CASE(NN) \
-    case NN: return pick_lines<R, NN>();
+    case NN: return rows ? pick_lines<R, NN, true>() : pick_lines<R, NN, false>();
         GPE_FOR_EACH_N(GPE_CASE)
 #undef GPE_CASE
     default: return 0;
