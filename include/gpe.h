@@ -129,6 +129,18 @@ int64_t gpe_spectrum_nshells(const gpe_plan *plan);
 gpe_status gpe_spectrum(gpe_plan *plan, const void *psi_dev, unsigned kinds, double *out_host,
                         int64_t nshells);
 
+/* Plan options (implementation choices, no counterpart in the paper).
+ *   GPE_OPT_TMA_STAGING  value 1 (default): tiles of the y and z sweeps are
+ *                        fetched by the tensor-memory accelerator when the
+ *                        grid allows it (n0 a multiple of the tile's line
+ *                        count, instances back to back in one array); value 0:
+ *                        every tile is fetched by per-thread asynchronous
+ *                        copies.  Results are bit-identical either way.
+ * Returns GPE_EINVAL for an unknown option or value.  Takes effect at the next
+ * launch; not synchronising. */
+enum gpe_option { GPE_OPT_TMA_STAGING = 1 };
+gpe_status gpe_plan_set_option(gpe_plan *plan, int option, int64_t value);
+
 /* Tracing (profiling aid, no counterpart in the paper).  While enabled, every
  * kernel launch the plan makes is bracketed by two CUDA events on the plan
  * stream and filed under a kind such as "x512:I-NR-F" (axis, line length, and

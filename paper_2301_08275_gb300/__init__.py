@@ -31,7 +31,7 @@ EXPORTS = ["gpe_plan_create", "gpe_plan_destroy", "gpe_step_real", "gpe_step_rea
            "gpe_trace_enable", "gpe_trace_count", "gpe_trace_read", "gpe_norm_energy_noalloc",
            "gpe_batch_create", "gpe_batch_destroy", "gpe_batch_step_real", "gpe_batch_norm_energy",
            "gpe_batch_groups", "gpe_server_create", "gpe_server_destroy", "gpe_serve_submit", "gpe_serve_poll",
-           "gpe_server_stats"]
+           "gpe_server_stats", "gpe_plan_set_option"]
 
 
 class GpeError(RuntimeError):
@@ -121,6 +121,7 @@ def lib():
         L.gpe_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_size_t)]
         L.gpe_trace_enable.argtypes = [vp, ctypes.c_int]
+        L.gpe_plan_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_int64]
         L.gpe_trace_count.argtypes = [vp]
         L.gpe_trace_read.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t,
                                      ctypes.POINTER(i64), dp]
@@ -202,6 +203,13 @@ def gpe_norm_energy_noalloc(desc, psi_ptr, stream=None):
     _check(lib().gpe_norm_energy_noalloc(ctypes.byref(desc), ctypes.c_void_p(psi_ptr),
                                          ctypes.c_void_p(stream or 0), _dptr(out)))
     return out
+
+
+GPE_OPT_TMA_STAGING = 1
+
+
+def gpe_plan_set_option(plan, option, value):
+    _check(lib().gpe_plan_set_option(plan, int(option), int(value)))
 
 
 def gpe_trace_enable(plan, enable=True):
@@ -310,6 +318,9 @@ class Plan:
 
     def spectrum(self, psi, kinds=GPE_SPEC_INC | GPE_SPEC_COMP):
         return gpe_spectrum(self._h, self._ptr(psi), kinds, self.batch)
+
+    def set_option(self, option, value):
+        gpe_plan_set_option(self._h, option, value)
 
     def trace(self, enable=True):
         gpe_trace_enable(self._h, enable)

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -21,16 +22,16 @@
 #include "gpe_internal.h"
 
 namespace gpe {
-cudaError_t launch_pass_f32(bool rows, const PassArgs &a, cudaStream_t st);
-cudaError_t launch_pass_f64(bool rows, const PassArgs &a, cudaStream_t st);
+cudaError_t launch_pass_f32(bool rows, const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap);
+cudaError_t launch_pass_f64(bool rows, const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap);
 cudaError_t launch_line1d_f32(const Line1DArgs &a, cudaStream_t st);
 cudaError_t launch_line1d_f64(const Line1DArgs &a, cudaStream_t st);
 int lines_per_tile_f32(bool rows, int n);
 int lines_per_tile_f64(bool rows, int n);
 
-cudaError_t launch_pass(int prec, bool rows, const PassArgs &a, cudaStream_t st)
+cudaError_t launch_pass(int prec, bool rows, const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap)
 {
-    return prec == GPE_C64 ? launch_pass_f32(rows, a, st) : launch_pass_f64(rows, a, st);
+    return prec == GPE_C64 ? launch_pass_f32(rows, a, st, tmap) : launch_pass_f64(rows, a, st, tmap);
 }
 int pass_lines_per_tile(int prec, bool rows, int n)
 {
@@ -111,7 +112,14 @@ struct gpe_plan {
     std::vector<cudaEvent_t> event_pool;
     std::vector<std::string> kinds;
     std::map<std::string, std::pair<int64_t, double>> totals;
+    // tensor maps of the swept array for the strided axes, rebuilt when the
+    // array, axis or instance count changes
+    struct Tmap { const void *ptr = nullptr; int64_t batch = 0; bool ok = false; CUtensorMap map; };
+    Tmap tmaps[3];
+    bool use_tma = true;
 };
+
+static gpe_status check_err(gpe_plan *p);
 
 struct DeviceGuard {
     int prev = -1;
@@ -558,10 +566,76 @@ static void set_nreal(const gpe_plan *p, PassArgs &a, bool full)
     a.nl_c = full ? p->dt : 0.5 * p->dt;
 }
 
-static gpe_status run(gpe_plan *p, const PassArgs &a)
+// ------------------------------------------------------------------ tensor maps
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (the library links no driver stub)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled()
 {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> g(mu);
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    }
+    return fn;
+}
+
+// Tensor map of `batch` back-to-back instances at ptr, viewed as the 4D array
+// [batch][n2][n1][n0] of 8-byte elements (complex128 points are two of them
+// along n0), with a box of L lines by `box` points along `axis` (1 or 2).
+static bool make_tmap(const gpe_plan *p, int axis, const void *ptr, int64_t batch, int L, int box, CUtensorMap *m)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const int64_t w = (int64_t)(p->csize / 8);        // 8-byte elements per point
+    cuuint64_t dim[4] = {(cuuint64_t)(p->n[0] * w), (cuuint64_t)p->n[1], (cuuint64_t)p->n[2], (cuuint64_t)batch};
+    cuuint64_t stride[3] = {(cuuint64_t)(p->n[0] * p->csize), (cuuint64_t)(p->n[0] * p->n[1] * p->csize),
+                            (cuuint64_t)(p->N * p->csize)};
+    cuuint32_t boxd[4] = {(cuuint32_t)(L * w), axis == 1 ? (cuuint32_t)box : 1u, axis == 2 ? (cuuint32_t)box : 1u, 1u};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, const_cast<void *>(ptr), dim, stride, boxd, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+static gpe_status run(gpe_plan *p, const PassArgs &a_in)
+{
+    PassArgs a = a_in;
+    a.err = p->err;
+    const CUtensorMap *tm = nullptr;
+    // strided sweeps over one array of back-to-back instances, with whole
+    // tiles of consecutive x lines, take the copy-engine staging
+    if (p->use_tma && a.axis >= 1 && a.src && !a.inst_ptr && (a.dst == nullptr || a.dst == a.src)) {
+        const int L = pass_lines_per_tile(p->prec, false, a.nax);
+        const int box = a.nax < 256 ? a.nax : 256;
+        const int64_t batch = a.lines_total / (p->N / p->n[a.axis]);
+        if (p->n[0] % L == 0 && ((uintptr_t)a.src) % 16 == 0) {
+            gpe_plan::Tmap &c = p->tmaps[a.axis];
+            if (!c.ok || c.ptr != a.src || c.batch != batch) {
+                c.ok = make_tmap(p, a.axis, a.src, batch, L, box, &c.map);
+                c.ptr = a.src;
+                c.batch = batch;
+            }
+            if (c.ok) {
+                tm = &c.map;
+                a.tma_box = box;
+                a.tma_chunks = a.nax / box;
+            }
+        }
+    }
     TraceScope ts(p, pass_kind(a));
-    cudaError_t e = launch_pass(p->prec, a.axis == 0, a, p->st);
+    cudaError_t e = launch_pass(p->prec, a.axis == 0, a, p->st, tm);
     if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("pass launch: ") + cudaGetErrorString(e));
     return GPE_OK;
 }
@@ -664,8 +738,7 @@ extern "C" gpe_status gpe_step_real_host(gpe_plan *p, void *psi_host, int64_t ns
     GPE_CUDA(cudaMemcpyAsync(p->host_buf, psi_host, bytes, cudaMemcpyHostToDevice, p->st));
     GPE_TRY(step_real_dev(p, p->host_buf, nsteps));
     GPE_CUDA(cudaMemcpyAsync(psi_host, p->host_buf, bytes, cudaMemcpyDeviceToHost, p->st));
-    GPE_CUDA(cudaStreamSynchronize(p->st));
-    return GPE_OK;
+    return check_err(p);
 }
 
 // ------------------------------------------------------------------ diagnostics
@@ -689,11 +762,22 @@ static gpe_status diag_dev(gpe_plan *p, const void *psi)
     return GPE_OK;
 }
 
+// copy results out; the stream is synchronised and the device error word checked
 static gpe_status copy_out(gpe_plan *p, const double *dev, size_t count, double *host)
 {
     GPE_CUDA(cudaMemcpyAsync(host, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, p->st));
-    GPE_CUDA(cudaStreamSynchronize(p->st));
-    return GPE_OK;
+    return check_err(p);
+}
+
+extern "C" gpe_status gpe_plan_set_option(gpe_plan *p, int option, int64_t value)
+{
+    if (!p) return fail(GPE_EINVAL, "NULL plan");
+    if (option == GPE_OPT_TMA_STAGING) {
+        if (value != 0 && value != 1) return fail(GPE_EINVAL, "GPE_OPT_TMA_STAGING takes 0 or 1");
+        p->use_tma = value != 0;
+        return GPE_OK;
+    }
+    return fail(GPE_EINVAL, "unknown plan option");
 }
 
 extern "C" gpe_status gpe_norm_energy(gpe_plan *p, const void *psi, double *out)
@@ -800,6 +884,7 @@ static gpe_status check_err(gpe_plan *p)
     if (h) {
         cudaMemsetAsync(p->err, 0, sizeof(int), p->st);
         cudaStreamSynchronize(p->st);
+        if (h & ERR_TMA_TIMEOUT) return fail(GPE_ETIMEOUT, "a tile copy did not complete within the wait limit");
         return fail(GPE_ENUMERIC, "norm became zero or non-finite during imaginary time");
     }
     return GPE_OK;

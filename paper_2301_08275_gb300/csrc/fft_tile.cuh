@@ -322,6 +322,35 @@ template <typename R, int N, int L, int LPT, bool SW = false> struct GTile {
         }
     }
 
+    // Twiddles in shared memory are laid out pass by pass: pass p (Ns > 1)
+    // owns (r-1)*Ns entries at tw_off(p), entry (m-1)*Ns + k = W_{Ns r}^(m k).
+    // Lanes with consecutive k then read consecutive 16-byte entries (no bank
+    // conflicts) and each thread's r-1 reads sit at constant offsets.
+    __host__ __device__ static constexpr int tw_off(int p)
+    {
+        return p <= 1 ? 0 : tw_off(p - 1) + Radix<N>::ns(p - 1) * (Radix<N>::radix(p - 1) - 1);
+    }
+    static constexpr int TWN = tw_off(Radix<N>::P);
+    // fill the pass-ordered table from the natural one (W_N^t, t < N)
+    __device__ __forceinline__ static void load_twiddles(U *tws, const U *__restrict__ twg, int t, int nt)
+    {
+        for (int idx = t; idx < TWN; idx += nt) tws[idx] = twg[tw_src<1>(idx)];
+    }
+    template <int p> __device__ __forceinline__ static int tw_src(int idx)
+    {
+        if constexpr (p >= Radix<N>::P) {
+            return 0;
+        } else {
+            constexpr int ns = Radix<N>::ns(p), r = Radix<N>::radix(p);
+            const int rel = idx - tw_off(p);
+            if (rel < ns * (r - 1)) {
+                const int m = rel / ns + 1, k = rel % ns;
+                return m * k * (N / (ns * r));
+            }
+            return tw_src<p + 1>(idx);
+        }
+    }
+
     template <int DIR, int p>
     __device__ __forceinline__ static void pass(C (&v)[LPT][E], C *sm, int tl, int l0, const U *__restrict__ tw)
     {
@@ -347,9 +376,10 @@ template <typename R, int N, int L, int LPT, bool SW = false> struct GTile {
 #pragma unroll
                 for (int m = 0; m < r; ++m) x[ln][m] = v[ln][q + m * B];
             if constexpr (Ns > 1) {
+                const U *twk = tw + tw_off(p) + k;
 #pragma unroll
                 for (int m = 1; m < r; ++m) {
-                    const U w = tw[m * k * (N / (Ns * r))];
+                    const U w = twk[(m - 1) * Ns];
 #pragma unroll
                     for (int ln = 0; ln < LPT; ++ln) x[ln][m] = umul<(DIR > 0)>(x[ln][m], w);
                 }

@@ -1,5 +1,6 @@
 // gpe_internal.h - launch descriptors shared by the library's translation units.
 #pragma once
+#include <cuda.h>            // CUtensorMap (type only; the driver entry point is fetched at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -64,13 +65,24 @@ struct PassArgs {
     // diagnostics geometry
     const double *gamma;   // [batch][3]
     double lo[3], h[3], kf[3];   // box corner, spacing, 2 pi / len per axis
+    // tile staging by the tensor-memory accelerator (strided axes only): when
+    // tma_chunks > 0 each tile is fetched as tma_chunks boxes of tma_box points
+    // along the axis through the tensor map passed beside these arguments
+    int tma_chunks, tma_box;
+    int *err;              // device error word (bit ERR_TMA_TIMEOUT), may be NULL
+};
+
+enum : int {
+    ERR_NUMERIC = 1,       // non-finite or zero norm in a renormalisation
+    ERR_TMA_TIMEOUT = 2,   // a tile copy did not complete within the wait limit
 };
 
 // record the thread-local message returned by gpe_last_error()
 void set_last_error(const char *msg);
 
 // launch one pass; returns cudaSuccess or the launch error
-cudaError_t launch_pass(int prec, bool rows, const PassArgs &a, cudaStream_t st);
+// tmap: tensor map of the swept array when a.tma_chunks > 0, else NULL
+cudaError_t launch_pass(int prec, bool rows, const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap = nullptr);
 int pass_lines_per_tile(int prec, bool rows, int n);
 
 // whole 1D steps with each line (instance) resident on chip for all steps

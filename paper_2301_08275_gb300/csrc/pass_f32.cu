@@ -6,9 +6,9 @@ namespace gpe {
 
 cudaError_t launch_pass_rows_f32(const PassArgs &a, cudaStream_t st);
 
-cudaError_t launch_pass_f32(bool rows, const PassArgs &a, cudaStream_t st)
+cudaError_t launch_pass_f32(bool rows, const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap)
 {
-    return rows ? launch_pass_rows_f32(a, st) : launch_pass_r<float, false>(a, st);
+    return rows ? launch_pass_rows_f32(a, st) : launch_pass_r<float, false>(a, st, tmap);
 }
 cudaError_t launch_line1d_f32(const Line1DArgs &a, cudaStream_t st) { return launch_line1d_r<float>(a, st); }
 int lines_per_tile_f32(bool rows, int n) { return lines_per_tile_r<float>(rows, n); }

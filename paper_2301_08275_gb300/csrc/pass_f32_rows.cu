@@ -3,6 +3,6 @@
 
 namespace gpe {
 
-cudaError_t launch_pass_rows_f32(const PassArgs &a, cudaStream_t st) { return launch_pass_r<float, true>(a, st); }
+cudaError_t launch_pass_rows_f32(const PassArgs &a, cudaStream_t st) { return launch_pass_r<float, true>(a, st, nullptr); }
 
 }  // namespace gpe

@@ -30,6 +30,15 @@ __device__ __forceinline__ double2 phase_offset(double th)
     sincos(0.5 * th, &s, &c);
     return mk(-2.0 * s * s, -2.0 * s * c);
 }
+// short form for |th| <= 1/16: truncation below 1e-12 (sin) and 1e-14 (cos),
+// so the modulus of 1 + w stays one to about 1e-13
+__device__ __forceinline__ float2 phase_offset_small(float th)
+{
+    const float u = th * th;
+    const float cm = u * fmaf(u, fmaf(u, -1.38888889e-3f, 4.16666667e-2f), -0.5f);
+    const float sn = th * fmaf(u, fmaf(u, 8.33333333e-3f, -1.66666667e-1f), 1.0f);
+    return mk(cm, -sn);
+}
 __device__ __forceinline__ float2 phase_offset(float th)
 {
     if (fabsf(th) <= 0.5f) {
@@ -147,9 +156,30 @@ __device__ __forceinline__ void point_op(int op, typename CT<R>::C (&v)[E], cons
         const U *v1 = static_cast<const U *>(a.vt_o1);
         const U f0 = v0 ? v0[(int64_t)ti * a.o0n + c0] : U{};
         const U f1 = v1 ? v1[(int64_t)ti * a.o1n + c1] : U{};
+        R th[E];
+        R mx = (R)0;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            C x = cmadd1(v[e], phase_offset(gc * cabs2(v[e])));
+            th[e] = gc * cabs2(v[e]);
+            mx = fmax(mx, fabs(th[e]));
+        }
+        // the whole warp takes the short series when all its angles are small
+        // (the usual case: dt |V + g|psi|^2| is far below 1/16)
+        bool small = false;
+        if constexpr (sizeof(R) == 4) {
+            small = __all_sync(__activemask(), mx <= 0.0625f);
+            if (small) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) v[e] = cmadd1(v[e], phase_offset_small(th[e]));
+            }
+        }
+        if (!small) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = cmadd1(v[e], phase_offset(th[e]));
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            C x = v[e];
             if (vax) x = uomul(x, vax[(int64_t)ti * a.nax + tl + TPL * e]);
             if (v0) x = uomul(x, f0);
             if (v1) x = uomul(x, f1);
@@ -180,6 +210,61 @@ __device__ __forceinline__ void cp_async_point(void *smem, const double2 *g)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(g));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+
+// ---- tensor-memory-accelerator tile copies with an mbarrier per buffer
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// make the initialised barriers visible to the copy engine
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// order this CTA's earlier ordinary shared-memory accesses before later copies into it
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+// wait for the given phase parity of a barrier, for at most ~2 s
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > 2000000000ull) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+        : "memory");
+}
 template <int K> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K)); }
 
 // Geometry of the line a thread works on in a given tile.
@@ -257,22 +342,57 @@ template <typename R, int N, int L, bool ROWS> constexpr int pass_min_blocks()
 template <typename R, int N, int L, bool ROWS>
 __global__ void __launch_bounds__(GTile<R, N, L, lines_per_thread<R>(), rows_split<R, N, ROWS>()>::NT,
                                   (pass_min_blocks<R, N, L, ROWS>()))
-    k_pass(const PassArgs a)
+    k_pass(const PassArgs a, const __grid_constant__ CUtensorMap tmap)
 {
     constexpr int LPT = lines_per_thread<R>();
     using T = GTile<R, N, L, LPT, rows_split<R, N, ROWS>()>;
     using C = typename T::C;
     using U = typename T::U;
     constexpr int E = T::E, TPL = T::TPL;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     C *buf0 = reinterpret_cast<C *>(smraw);
     C *buf1 = buf0 + T::SMEM_POINTS;
     double *red = reinterpret_cast<double *>(smraw + 2 * sizeof(C) * T::SMEM_POINTS);
     U *tw = reinterpret_cast<U *>(smraw + 2 * sizeof(C) * T::SMEM_POINTS + sizeof(double) * N * L / E);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smraw + 2 * sizeof(C) * T::SMEM_POINTS +
+                                                  sizeof(double) * N * L / E + sizeof(U) * N);
     const int t = threadIdx.x, l0 = (t % T::NP) * LPT, tl = t / T::NP;
-    for (int i = t; i < N; i += T::NT) tw[i] = static_cast<const U *>(a.tw)[i];
+    T::load_twiddles(tw, static_cast<const U *>(a.tw), t, T::NT);
 
-    auto stage = [&](int64_t tile, C *buf) {
+    // Strided tiles (point i of line l at i*L + l, the layout of a box of L
+    // lines by tma_box points) can be fetched by the copy engine: thread 0
+    // issues the boxes of a tile against the buffer's mbarrier and every
+    // thread waits on it.  Other tiles go through per-thread cp.async.
+    const bool tma = !ROWS && LPT == 1 && a.tma_chunks > 0;
+    if (tma) {
+        if (t == 0) {
+            mbar_init(&mbar[0], 1);
+            mbar_init(&mbar[1], 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+    }
+    int issued[2] = {0, 0};   // boxes sets issued into each buffer (thread 0)
+
+    auto stage = [&](int64_t tile, C *buf, int b) {
+        if (tma) {
+            if (t == 0 && tile < a.ntiles) {
+                const int64_t lg = tile * L;
+                const int inst = int(lg >> a.lg_lpi);
+                const int64_t li = lg & ((int64_t(1) << a.lg_lpi) - 1);
+                const int c0 = int(li & (a.o0n - 1)), c1 = int(li >> a.lg_o0);
+                const int x = c0 * (int)(sizeof(C) / 8);      // complex128 rows are pairs of doubles
+                fence_async_shared();
+                mbar_expect_tx(&mbar[b], (unsigned)(sizeof(C) * N * L));
+                for (int c = 0; c < a.tma_chunks; ++c) {
+                    const int pa = c * a.tma_box;
+                    if (a.axis == 1) tma_load_4d(buf + pa * L, &tmap, x, pa, c1, inst, &mbar[b]);
+                    else tma_load_4d(buf + pa * L, &tmap, x, c1, pa, inst, &mbar[b]);
+                }
+                ++issued[b];
+            }
+            return;
+        }
         if (tile < a.ntiles) {
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln) {
@@ -289,12 +409,23 @@ __global__ void __launch_bounds__(GTile<R, N, L, lines_per_thread<R>(), rows_spl
     };
 
     int64_t tile = blockIdx.x;
-    stage(tile, buf0);
-    stage(tile + gridDim.x, buf1);
-    for (int it = 0; tile < a.ntiles; ++it, tile += gridDim.x) {
+    stage(tile, buf0, 0);
+    stage(tile + gridDim.x, buf1, 1);
+    int it = 0;
+    bool aborted = false;
+    for (; tile < a.ntiles; ++it, tile += gridDim.x) {
         C *sm = (it & 1) ? buf1 : buf0;
-        cp_async_wait<1>();      // this tile's copies are done (the next tile's may still fly)
-        __syncthreads();
+        if (tma) {
+            // this tile's boxes have landed (the next tile's may still fly)
+            const bool ok = mbar_wait_bounded(&mbar[it & 1], (unsigned)(it >> 1) & 1u);
+            if (__syncthreads_or(!ok)) {
+                aborted = true;
+                break;
+            }
+        } else {
+            cp_async_wait<1>();      // this tile's copies are done (the next tile's may still fly)
+            __syncthreads();
+        }
         LineGeom g[LPT];
 #pragma unroll
         for (int ln = 0; ln < LPT; ++ln) g[ln] = line_geom<L>(a, tile, l0 + ln);
@@ -413,10 +544,21 @@ __global__ void __launch_bounds__(GTile<R, N, L, lines_per_thread<R>(), rows_spl
                 }
             }
         }
+        if (tma) fence_async_shared();   // this thread's accesses to the buffer precede the next copy into it
         __syncthreads();         // every thread is done with this buffer
-        stage(tile + 2 * (int64_t)gridDim.x, sm);
+        stage(tile + 2 * (int64_t)gridDim.x, sm, it & 1);
     }
-    cp_async_wait<0>();
+    if (!tma) {
+        cp_async_wait<0>();
+    } else if (aborted && t == 0) {
+        // report, then let the boxes still in flight land before the CTA exits
+        if (a.err) atomicOr(a.err, (int)ERR_TMA_TIMEOUT);
+        for (int b = 0; b < 2; ++b) {
+            int waited = b == 0 ? (it + 1) / 2 : it / 2;
+            for (; waited < issued[b]; ++waited)
+                if (!mbar_wait_bounded(&mbar[b], (unsigned)waited & 1u)) break;
+        }
+    }
 }
 
 // ------------------------------------------------------------------ 1D on chip
@@ -430,7 +572,7 @@ __global__ void __launch_bounds__(Tile<R, N, L, true>::NT) k_line1d(const Line1D
     using C = typename T::C;
     constexpr int E = T::E, TPL = T::TPL;
     using U = typename T::U;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
     double *red = reinterpret_cast<double *>(smraw + sizeof(C) * T::SMEM_POINTS);
     U *tw = reinterpret_cast<U *>(smraw + sizeof(C) * T::SMEM_POINTS + sizeof(double) * T::NT);
@@ -505,7 +647,7 @@ __global__ void __launch_bounds__(Tile<R, N, L, true>::NT) k_line1d(const Line1D
                 }
                 nrm = line_sum<L, TPL>(nrm, red, l, tl);
                 if (!(nrm > 0.0) || !isfinite(nrm)) {
-                    if (valid && tl == 0) atomicExch(a.err, 1);
+                    if (valid && tl == 0) atomicOr(a.err, (int)ERR_NUMERIC);
                     sc = (R)1;
                 } else {
                     sc = (R)sqrt(a.target_norm_over_dv / nrm);
@@ -550,19 +692,24 @@ static cudaError_t prepare(K kern, LaunchCache &lc, int nt, size_t smem, int *ca
     return cudaSuccess;
 }
 
-template <typename R, int N, bool ROWS> static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st)
+template <typename R, int N, bool ROWS>
+static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap)
 {
     constexpr int L = pick_lines<R, N, ROWS>();
     using T = GTile<R, N, L, lines_per_thread<R>(), rows_split<R, N, ROWS>()>;
     static LaunchCache lc;
+    static const CUtensorMap none = {};
     const size_t smem = 2 * sizeof(typename T::C) * T::SMEM_POINTS + sizeof(double) * (N * L / T::E) +
-                        sizeof(typename T::U) * N;
+                        sizeof(typename T::U) * N + 2 * sizeof(uint64_t);
+    if (a.tma_chunks > 0 && (ROWS || !tmap || (int64_t)a.tma_chunks * a.tma_box != N || a.tma_box > 256 ||
+                             a.axis < 1 || a.o0n % L != 0))
+        return cudaErrorInvalidValue;
     int cap = 0;
     cudaError_t e = prepare(k_pass<R, N, L, ROWS>, lc, T::NT, smem, &cap);
     if (e != cudaSuccess) return e;
     if (a.ntiles <= 0) return cudaSuccess;
     const int grid = (int)(a.ntiles < cap ? a.ntiles : cap);
-    k_pass<R, N, L, ROWS><<<grid, T::NT, smem, st>>>(a);
+    k_pass<R, N, L, ROWS><<<grid, T::NT, smem, st>>>(a, tmap ? *tmap : none);
     return cudaGetLastError();
 }
 
@@ -584,11 +731,12 @@ template <typename R, int N> static cudaError_t launch_line1d_t(const Line1DArgs
 
 #define GPE_FOR_EACH_N(X) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
 
-template <typename R, bool ROWS> static cudaError_t launch_pass_r(const PassArgs &a, cudaStream_t st)
+template <typename R, bool ROWS>
+static cudaError_t launch_pass_r(const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap)
 {
     switch (a.nax) {
 #define GPE_CASE(NN) \
-    case NN: return launch_pass_t<R, NN, ROWS>(a, st);
+    case NN: return launch_pass_t<R, NN, ROWS>(a, st, tmap);
         GPE_FOR_EACH_N(GPE_CASE)
 #undef GPE_CASE
     default: return cudaErrorInvalidValue;

@@ -304,3 +304,48 @@ def test_invalid_arguments_are_reported(gpe):
     with pytest.raises(gpe.GpeError):
         gpe.gpe_step_real(p._h, x.data_ptr(), -1)
     p.close()
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_nonlinear_phase_over_all_angle_ranges(gpe, orc, prec):
+    """A narrow dense cloud at large g: nonlinear angles above 1/2 at the centre
+    (library sincos), between 1/16 and 1/2 on the flanks (long series) and
+    below 1/16 in the tails (short series), all in one grid."""
+    sp = gi.Spec(n=(64, 64), lo=(-6.0, -6.0), length=(12.0, 12.0), g=2000.0, dt=1e-3, gamma=(1.0, 1.0))
+    psi0 = gi.harmonic_gaussian(sp, seed=3, noise=0.01)
+    th = sp.g * sp.dt * np.abs(psi0) ** 2
+    assert th.max() > 0.5 and np.any((th > 0.0625) & (th < 0.5)) and np.any(th < 0.0625)
+    steps = 5
+    ref = P(orc, sp).step_real(psi0, steps)
+    pv = gpe.GPE_C128 if prec == "c128" else gpe.GPE_C64
+    out = gpu_real(gpe, sp, psi0, steps, pv)
+    assert rel(out, ref) < (TOL128 if prec == "c128" else 2e-5)
+
+
+@pytest.mark.parametrize("n,batch", [((64, 32, 16), 1), ((32, 16, 8), 3), ((512, 8, 256), 1), ((64, 256), 2),
+                                     ((2048, 4), 1), ((8, 64, 16), 1), ((16, 512), 1)],
+                         ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else str(v))
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_copy_engine_staging_is_bit_identical(gpe, n, batch, prec):
+    """Tiles fetched by the tensor-memory accelerator and by per-thread copies
+    feed the same arithmetic: steps, imaginary-time steps and diagnostics agree
+    bit for bit (grids include ones where n0 is too small for the copy engine)."""
+    import torch
+    sp = _spec(n)
+    pv = gpe.GPE_C128 if prec == "c128" else gpe.GPE_C64
+    dt = np.complex128 if prec == "c128" else np.complex64
+    psi0 = np.stack([gi.random_field(sp, seed=11 + b, smooth=0.05) for b in range(batch)]).astype(dt)
+    outs = []
+    for tma in (1, 0):
+        p = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma[: sp.ndim], prec=pv, batch=batch)
+        p.set_option(gpe.GPE_OPT_TMA_STAGING, tma)
+        x = torch.from_numpy(psi0.copy()).cuda()
+        p.step_real(x, 3)
+        e = p.norm_energy(x)
+        y = torch.from_numpy(psi0.copy()).cuda()
+        p.step_imag(y, 2, etol=0.0, check_every=2)
+        torch.cuda.synchronize()
+        outs.append((x.cpu().numpy(), y.cpu().numpy(), np.asarray(e)))
+        p.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
