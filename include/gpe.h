@@ -129,17 +129,42 @@ int64_t gpe_spectrum_nshells(const gpe_plan *plan);
 gpe_status gpe_spectrum(gpe_plan *plan, const void *psi_dev, unsigned kinds, double *out_host,
                         int64_t nshells);
 
-/* Plan options (implementation choices, no counterpart in the paper).
- *   GPE_OPT_TMA_STAGING  value 1 (default): tiles of the y and z sweeps are
- *                        fetched by the tensor-memory accelerator when the
- *                        grid allows it (n0 a multiple of the tile's line
- *                        count, instances back to back in one array); value 0:
- *                        every tile is fetched by per-thread asynchronous
- *                        copies.  Results are bit-identical either way.
- * Returns GPE_EINVAL for an unknown option or value.  Takes effect at the next
- * launch; not synchronising. */
-enum gpe_option { GPE_OPT_TMA_STAGING = 1 };
+/* Plan options (implementation choices, no counterpart in the paper).  Every
+ * option takes 0 or 1; results are bit-identical for every setting (each
+ * line's arithmetic does not depend on them), only the speed changes.
+ *   GPE_OPT_TMA_STAGING  1 (default): tiles of the y and z sweeps are fetched
+ *                        by the tensor-memory accelerator when the grid allows
+ *                        it (n0 a multiple of the tile's line count, instances
+ *                        back to back in one array); 0: by per-thread
+ *                        asynchronous copies.  Sets both axes; GPE_OPT_TMA_Y /
+ *                        GPE_OPT_TMA_Z set one.
+ *   GPE_OPT_TILE_X/Y/Z   tile shape of the sweeps along x, y, z (0 default,
+ *                        1 the alternative compiled shape: different lines per
+ *                        tile and CTAs per SM).
+ * gpe_plan_set_option returns GPE_EINVAL for an unknown option or value and
+ * takes effect at the next launch; gpe_plan_get_option reads one back. */
+enum gpe_option {
+    GPE_OPT_TMA_STAGING = 1,
+    GPE_OPT_TILE_X = 2,
+    GPE_OPT_TILE_Y = 3,
+    GPE_OPT_TILE_Z = 4,
+    GPE_OPT_TMA_Y = 5,
+    GPE_OPT_TMA_Z = 6
+};
 gpe_status gpe_plan_set_option(gpe_plan *plan, int option, int64_t value);
+gpe_status gpe_plan_get_option(const gpe_plan *plan, int option, int64_t *value);
+
+/* Autotuner (no counterpart in the paper): for every axis the plan sweeps,
+ * times each tile shape (and, on y/z, each staging mode unless
+ * GPE_TUNE_NO_TMA) on a scratch copy of psi_dev (the caller's array is only
+ * read), `reps` launches per candidate of the pass that the steady real-time
+ * step makes along that axis, and sets the options of the fastest.  Choices
+ * are remembered per grid, precision and instance count for the life of the
+ * process, so later plans of the same shape tune without timing.  Needs one
+ * state-sized device scratch array for the duration of the call; synchronises
+ * the plan stream.  1D plans have nothing to tune (GPE_OK). */
+#define GPE_TUNE_NO_TMA 1
+gpe_status gpe_plan_autotune(gpe_plan *plan, const void *psi_dev, int reps, int flags);
 
 /* Tracing (profiling aid, no counterpart in the paper).  While enabled, every
  * kernel launch the plan makes is bracketed by two CUDA events on the plan

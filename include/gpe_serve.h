@@ -25,8 +25,10 @@ extern "C" {
 typedef struct gpe_batch gpe_batch;
 
 /* count instance descriptions (each with batch == 1 and no per-instance
- * arrays).  Instances are grouped; each group owns one plan.  The batch
- * enqueues on cuda_stream (NULL: legacy default stream). */
+ * arrays).  Instances are grouped; each group owns one plan, whose tile
+ * shapes are chosen by gpe_plan_autotune on the group's grid (per-thread
+ * staging; one scratch array of the group's size while the call runs).  The
+ * batch enqueues on cuda_stream (NULL: legacy default stream). */
 gpe_status gpe_batch_create(const gpe_plan_desc *descs, int count, void *cuda_stream, gpe_batch **out);
 gpe_status gpe_batch_destroy(gpe_batch *batch);
 

@@ -31,7 +31,8 @@ EXPORTS = ["gpe_plan_create", "gpe_plan_destroy", "gpe_step_real", "gpe_step_rea
            "gpe_trace_enable", "gpe_trace_count", "gpe_trace_read", "gpe_norm_energy_noalloc",
            "gpe_batch_create", "gpe_batch_destroy", "gpe_batch_step_real", "gpe_batch_norm_energy",
            "gpe_batch_groups", "gpe_server_create", "gpe_server_destroy", "gpe_serve_submit", "gpe_serve_poll",
-           "gpe_server_stats", "gpe_plan_set_option"]
+           "gpe_server_stats", "gpe_plan_set_option", "gpe_plan_get_option",
+           "gpe_plan_autotune"]
 
 
 class GpeError(RuntimeError):
@@ -122,6 +123,8 @@ def lib():
                                        ctypes.POINTER(ctypes.c_size_t)]
         L.gpe_trace_enable.argtypes = [vp, ctypes.c_int]
         L.gpe_plan_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_int64]
+        L.gpe_plan_get_option.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
+        L.gpe_plan_autotune.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
         L.gpe_trace_count.argtypes = [vp]
         L.gpe_trace_read.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t,
                                      ctypes.POINTER(i64), dp]
@@ -205,11 +208,23 @@ def gpe_norm_energy_noalloc(desc, psi_ptr, stream=None):
     return out
 
 
-GPE_OPT_TMA_STAGING = 1
+GPE_OPT_TMA_STAGING, GPE_OPT_TILE_X, GPE_OPT_TILE_Y, GPE_OPT_TILE_Z, GPE_OPT_TMA_Y, GPE_OPT_TMA_Z = 1, 2, 3, 4, 5, 6
+GPE_TUNE_NO_TMA = 1
 
 
 def gpe_plan_set_option(plan, option, value):
     _check(lib().gpe_plan_set_option(plan, int(option), int(value)))
+
+
+def gpe_plan_get_option(plan, option):
+    v = ctypes.c_int64(0)
+    _check(lib().gpe_plan_get_option(plan, int(option), ctypes.byref(v)))
+    return v.value
+
+
+def gpe_plan_autotune(plan, psi_ptr, reps=3, flags=0):
+    """psi_ptr: device address of a state to time on (read only), or 0 for zeros."""
+    _check(lib().gpe_plan_autotune(plan, ctypes.c_void_p(psi_ptr or None), int(reps), int(flags)))
 
 
 def gpe_trace_enable(plan, enable=True):
@@ -321,6 +336,17 @@ class Plan:
 
     def set_option(self, option, value):
         gpe_plan_set_option(self._h, option, value)
+
+    def get_option(self, option):
+        return gpe_plan_get_option(self._h, option)
+
+    def autotune(self, psi=None, reps=3, flags=0):
+        """Time the tile shapes / staging modes on a scratch copy of psi (a CUDA
+        tensor, only read) and keep the fastest; returns the chosen options."""
+        gpe_plan_autotune(self._h, self._ptr(psi) if psi is not None else 0, reps, flags)
+        return {name: self.get_option(opt) for name, opt in
+                (("tile_x", GPE_OPT_TILE_X), ("tile_y", GPE_OPT_TILE_Y), ("tile_z", GPE_OPT_TILE_Z),
+                 ("tma_y", GPE_OPT_TMA_Y), ("tma_z", GPE_OPT_TMA_Z))}
 
     def trace(self, enable=True):
         gpe_trace_enable(self._h, enable)

@@ -22,20 +22,20 @@
 #include "gpe_internal.h"
 
 namespace gpe {
-cudaError_t launch_pass_f32(bool rows, const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap);
-cudaError_t launch_pass_f64(bool rows, const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap);
+cudaError_t launch_pass_f32(bool rows, int var, const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap);
+cudaError_t launch_pass_f64(bool rows, int var, const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap);
 cudaError_t launch_line1d_f32(const Line1DArgs &a, cudaStream_t st);
 cudaError_t launch_line1d_f64(const Line1DArgs &a, cudaStream_t st);
-int lines_per_tile_f32(bool rows, int n);
-int lines_per_tile_f64(bool rows, int n);
+int lines_per_tile_f32(bool rows, int n, int var);
+int lines_per_tile_f64(bool rows, int n, int var);
 
-cudaError_t launch_pass(int prec, bool rows, const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap)
+cudaError_t launch_pass(int prec, bool rows, const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap, int var)
 {
-    return prec == GPE_C64 ? launch_pass_f32(rows, a, st, tmap) : launch_pass_f64(rows, a, st, tmap);
+    return prec == GPE_C64 ? launch_pass_f32(rows, var, a, st, tmap) : launch_pass_f64(rows, var, a, st, tmap);
 }
-int pass_lines_per_tile(int prec, bool rows, int n)
+int pass_lines_per_tile(int prec, bool rows, int n, int var)
 {
-    return prec == GPE_C64 ? lines_per_tile_f32(rows, n) : lines_per_tile_f64(rows, n);
+    return prec == GPE_C64 ? lines_per_tile_f32(rows, n, var) : lines_per_tile_f64(rows, n, var);
 }
 cudaError_t launch_line1d(int prec, const Line1DArgs &a, cudaStream_t st)
 {
@@ -114,9 +114,10 @@ struct gpe_plan {
     std::map<std::string, std::pair<int64_t, double>> totals;
     // tensor maps of the swept array for the strided axes, rebuilt when the
     // array, axis or instance count changes
-    struct Tmap { const void *ptr = nullptr; int64_t batch = 0; bool ok = false; CUtensorMap map; };
+    struct Tmap { const void *ptr = nullptr; int64_t batch = 0; int lines = 0; bool ok = false; CUtensorMap map; };
     Tmap tmaps[3];
-    bool use_tma = true;
+    bool use_tma[3] = {true, true, true};   // copy-engine staging per axis (strided axes only)
+    int tile_var[3] = {0, 0, 0};            // tile shape per axis
 };
 
 static gpe_status check_err(gpe_plan *p);
@@ -519,7 +520,7 @@ static PassArgs make_pass(const gpe_plan *p, int axis, const void *src, void *ds
     a.o1n = (int)p->n[o1];
     a.lg_o0 = ilog2_64(p->n[o0]);
     a.lines_total = batch * lpi;
-    const int L = pass_lines_per_tile(p->prec, axis == 0, a.nax);
+    const int L = pass_lines_per_tile(p->prec, axis == 0, a.nax, p->tile_var[axis]);
     a.ntiles = (a.lines_total + L - 1) / L;
     a.tw = p->tw[axis];
     const bool h0 = o0 < p->ndim, h1 = o1 < p->ndim;
@@ -616,16 +617,18 @@ static gpe_status run(gpe_plan *p, const PassArgs &a_in)
     const CUtensorMap *tm = nullptr;
     // strided sweeps over one array of back-to-back instances, with whole
     // tiles of consecutive x lines, take the copy-engine staging
-    if (p->use_tma && a.axis >= 1 && a.src && !a.inst_ptr && (a.dst == nullptr || a.dst == a.src)) {
-        const int L = pass_lines_per_tile(p->prec, false, a.nax);
+    const int var = p->tile_var[a.axis];
+    if (p->use_tma[a.axis] && a.axis >= 1 && a.src && !a.inst_ptr && (a.dst == nullptr || a.dst == a.src)) {
+        const int L = pass_lines_per_tile(p->prec, false, a.nax, var);
         const int box = a.nax < 256 ? a.nax : 256;
         const int64_t batch = a.lines_total / (p->N / p->n[a.axis]);
         if (p->n[0] % L == 0 && ((uintptr_t)a.src) % 16 == 0) {
             gpe_plan::Tmap &c = p->tmaps[a.axis];
-            if (!c.ok || c.ptr != a.src || c.batch != batch) {
+            if (!c.ok || c.ptr != a.src || c.batch != batch || c.lines != L) {
                 c.ok = make_tmap(p, a.axis, a.src, batch, L, box, &c.map);
                 c.ptr = a.src;
                 c.batch = batch;
+                c.lines = L;
             }
             if (c.ok) {
                 tm = &c.map;
@@ -635,7 +638,7 @@ static gpe_status run(gpe_plan *p, const PassArgs &a_in)
         }
     }
     TraceScope ts(p, pass_kind(a));
-    cudaError_t e = launch_pass(p->prec, a.axis == 0, a, p->st, tm);
+    cudaError_t e = launch_pass(p->prec, a.axis == 0, a, p->st, tm, var);
     if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("pass launch: ") + cudaGetErrorString(e));
     return GPE_OK;
 }
@@ -772,12 +775,161 @@ static gpe_status copy_out(gpe_plan *p, const double *dev, size_t count, double 
 extern "C" gpe_status gpe_plan_set_option(gpe_plan *p, int option, int64_t value)
 {
     if (!p) return fail(GPE_EINVAL, "NULL plan");
+    if (value != 0 && value != 1) return fail(GPE_EINVAL, "plan options take 0 or 1");
     if (option == GPE_OPT_TMA_STAGING) {
-        if (value != 0 && value != 1) return fail(GPE_EINVAL, "GPE_OPT_TMA_STAGING takes 0 or 1");
-        p->use_tma = value != 0;
+        for (int a = 0; a < 3; ++a) p->use_tma[a] = value != 0;
+        return GPE_OK;
+    }
+    if (option >= GPE_OPT_TILE_X && option <= GPE_OPT_TILE_Z) {
+        p->tile_var[option - GPE_OPT_TILE_X] = (int)value;
+        return GPE_OK;
+    }
+    if (option == GPE_OPT_TMA_Y || option == GPE_OPT_TMA_Z) {
+        p->use_tma[option - GPE_OPT_TMA_Y + 1] = value != 0;
         return GPE_OK;
     }
     return fail(GPE_EINVAL, "unknown plan option");
+}
+
+extern "C" gpe_status gpe_plan_get_option(const gpe_plan *p, int option, int64_t *value)
+{
+    if (!p || !value) return fail(GPE_EINVAL, "NULL argument");
+    if (option == GPE_OPT_TMA_STAGING) *value = (p->use_tma[1] || p->use_tma[2]) ? 1 : 0;
+    else if (option >= GPE_OPT_TILE_X && option <= GPE_OPT_TILE_Z) *value = p->tile_var[option - GPE_OPT_TILE_X];
+    else if (option == GPE_OPT_TMA_Y || option == GPE_OPT_TMA_Z) *value = p->use_tma[option - GPE_OPT_TMA_Y + 1] ? 1 : 0;
+    else return fail(GPE_EINVAL, "unknown plan option");
+    return GPE_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+namespace {
+struct TuneVal {
+    int var[3];
+    bool tma[3];
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneVal> g_tune;   // choices per grid/precision/instances/flags, process-wide
+}  // namespace
+
+static std::string tune_key(const gpe_plan *p, int64_t batch, int flags)
+{
+    char buf[160];
+    snprintf(buf, sizeof(buf), "%d/%d/%lldx%lldx%lld/%lld/%d", p->prec, p->ndim, (long long)p->n[0],
+             (long long)p->n[1], (long long)p->n[2], (long long)batch, flags);
+    return buf;
+}
+
+// the pass that the steady real-time step makes along `axis`
+static PassArgs steady_pass(const gpe_plan *p, int axis, void *buf, int64_t batch)
+{
+    PassArgs a = make_pass(p, axis, buf, buf, batch);
+    const int piv = p->ndim - 1;
+    if (axis == 0) {
+        a.fft1 = +1;
+        a.op_mid = OP_NREAL;
+        set_nreal(p, a, true);
+        a.fft2 = -1;
+    } else if (axis == piv) {
+        a.fft1 = -1;
+        a.op_mid = OP_KREAL;
+        a.fft2 = +1;
+    } else {
+        a.fft1 = +1;
+    }
+    return a;
+}
+
+static void apply_tune(gpe_plan *p, const TuneVal &v)
+{
+    for (int a = 0; a < 3; ++a) {
+        p->tile_var[a] = v.var[a];
+        p->use_tma[a] = v.tma[a];
+    }
+}
+
+extern "C" gpe_status gpe_plan_autotune(gpe_plan *p, const void *psi, int reps, int flags)
+{
+    if (!p) return fail(GPE_EINVAL, "NULL plan");
+    if (psi && ((uintptr_t)psi) % 16 != 0) return fail(GPE_EINVAL, "psi must be 16-byte aligned");
+    if (reps < 1 || reps > 1000) return fail(GPE_EINVAL, "reps must be in [1, 1000]");
+    if (flags & ~GPE_TUNE_NO_TMA) return fail(GPE_EINVAL, "unknown autotune flag");
+    if (p->ndim == 1) return GPE_OK;
+    if (p->cur_count > 0) return fail(GPE_EINVAL, "plan is in use by a batch launch");
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return fail(GPE_ECUDA, "cannot select the plan's device");
+    const int64_t B = p->batch;
+    const std::string key = tune_key(p, B, flags);
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            apply_tune(p, it->second);
+            return GPE_OK;
+        }
+    }
+    const size_t bytes = (size_t)B * (size_t)p->N * p->csize;
+    void *buf = nullptr;
+    GPE_CUDA(cudaMalloc(&buf, bytes));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    gpe_status st = GPE_OK;
+    TuneVal best;
+    for (int a = 0; a < 3; ++a) {
+        best.var[a] = 0;
+        best.tma[a] = a >= 1 && !(flags & GPE_TUNE_NO_TMA);
+    }
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        st = fail(GPE_ECUDA, "cudaEventCreate failed");
+    if (st == GPE_OK && !psi && cudaMemsetAsync(buf, 0, bytes, p->st) != cudaSuccess)
+        st = fail(GPE_ECUDA, "cudaMemsetAsync failed");
+    for (int a = 0; a < p->ndim && st == GPE_OK; ++a) {
+        double best_ms = 1e300;
+        const int ntma = (a >= 1 && !(flags & GPE_TUNE_NO_TMA)) ? 2 : 1;
+        for (int var = 0; var < 2 && st == GPE_OK; ++var) {
+            for (int ti = 0; ti < ntma && st == GPE_OK; ++ti) {
+                p->tile_var[a] = var;
+                p->use_tma[a] = ntma == 2 && ti == 0;
+                double total = 0.0;
+                for (int r = 0; r <= reps && st == GPE_OK; ++r) {   // r = 0 warms up
+                    if (psi && cudaMemcpyAsync(buf, psi, bytes, cudaMemcpyDeviceToDevice, p->st) != cudaSuccess) {
+                        st = fail(GPE_ECUDA, "scratch copy failed");
+                        break;
+                    }
+                    cudaEventRecord(e0, p->st);
+                    st = run(p, steady_pass(p, a, buf, B));
+                    cudaEventRecord(e1, p->st);
+                    if (st != GPE_OK) break;
+                    float ms = 0.f;
+                    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                        st = fail(GPE_ECUDA, "timing the candidate failed");
+                        break;
+                    }
+                    if (r > 0) total += ms;
+                }
+                if (st == GPE_OK && total < best_ms) {
+                    best_ms = total;
+                    best.var[a] = var;
+                    best.tma[a] = p->use_tma[a];
+                }
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (st == GPE_OK) st = check_err(p);
+    if (st != GPE_OK) {
+        TuneVal d;
+        for (int a = 0; a < 3; ++a) {
+            d.var[a] = 0;
+            d.tma[a] = true;
+        }
+        apply_tune(p, d);
+        return st;
+    }
+    apply_tune(p, best);
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[key] = best;
+    return GPE_OK;
 }
 
 extern "C" gpe_status gpe_norm_energy(gpe_plan *p, const void *psi, double *out)

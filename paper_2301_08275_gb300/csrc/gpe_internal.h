@@ -81,9 +81,11 @@ enum : int {
 void set_last_error(const char *msg);
 
 // launch one pass; returns cudaSuccess or the launch error
-// tmap: tensor map of the swept array when a.tma_chunks > 0, else NULL
-cudaError_t launch_pass(int prec, bool rows, const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap = nullptr);
-int pass_lines_per_tile(int prec, bool rows, int n);
+// tmap: tensor map of the swept array when a.tma_chunks > 0, else NULL;
+// var: tile shape (0 or 1, see pass_kernels.cuh)
+cudaError_t launch_pass(int prec, bool rows, const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap = nullptr,
+                        int var = 0);
+int pass_lines_per_tile(int prec, bool rows, int n, int var = 0);
 
 // whole 1D steps with each line (instance) resident on chip for all steps
 struct Line1DArgs {

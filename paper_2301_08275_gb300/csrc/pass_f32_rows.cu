@@ -1,8 +1,11 @@
-// pass_f32_rows.cu - float instantiations of the x-axis (row) line-pass kernels.
+// pass_f32_rows.cu - float instantiations of the x-axis (row) line-pass kernels, tile shape 0.
 #include "pass_kernels.cuh"
 
 namespace gpe {
 
-cudaError_t launch_pass_rows_f32(const PassArgs &a, cudaStream_t st) { return launch_pass_r<float, true>(a, st, nullptr); }
+cudaError_t launch_pass_rows0_f32(const PassArgs &a, cudaStream_t st)
+{
+    return launch_pass_r<float, true, 0>(a, st, nullptr);
+}
 
 }  // namespace gpe

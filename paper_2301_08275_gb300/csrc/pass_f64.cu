@@ -1,16 +1,21 @@
-// pass_f64.cu - double instantiations of the strided line-pass (y, z axes) and
-// on-chip 1D kernels; the x-axis (row) passes are in pass_f64_rows.cu.
+// pass_f64.cu - double instantiations of the strided line-pass kernels (y, z
+// axes, tile shape 0) and the on-chip 1D kernels, and the pass dispatcher; the
+// other shapes are compiled in pass_f64_s1.cu, pass_f64_rows.cu and
+// pass_f64_rows1.cu.
 #include "pass_kernels.cuh"
 
 namespace gpe {
 
-cudaError_t launch_pass_rows_f64(const PassArgs &a, cudaStream_t st);
+cudaError_t launch_pass_s1_f64(const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap);
+cudaError_t launch_pass_rows0_f64(const PassArgs &a, cudaStream_t st);
+cudaError_t launch_pass_rows1_f64(const PassArgs &a, cudaStream_t st);
 
-cudaError_t launch_pass_f64(bool rows, const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap)
+cudaError_t launch_pass_f64(bool rows, int var, const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap)
 {
-    return rows ? launch_pass_rows_f64(a, st) : launch_pass_r<double, false>(a, st, tmap);
+    if (rows) return var ? launch_pass_rows1_f64(a, st) : launch_pass_rows0_f64(a, st);
+    return var ? launch_pass_s1_f64(a, st, tmap) : launch_pass_r<double, false, 0>(a, st, tmap);
 }
 cudaError_t launch_line1d_f64(const Line1DArgs &a, cudaStream_t st) { return launch_line1d_r<double>(a, st); }
-int lines_per_tile_f64(bool rows, int n) { return lines_per_tile_r<double>(rows, n); }
+int lines_per_tile_f64(bool rows, int n, int var) { return lines_per_tile_r<double>(rows, n, var); }
 
 }  // namespace gpe

@@ -54,30 +54,44 @@ __device__ __forceinline__ float2 phase_offset(float th)
     return mk(-2.0f * s * s, -2.0f * s * c);
 }
 
-// lines per tile.  Strided lines (y, z) of complex64: tiles of at most 8192
-// points and 16 adjacent lines, so that every point row of a tile is a
-// 128-byte segment (one CTA of <= 1024 threads per SM); with 8 lines (64-byte
-// pieces) the z sweep of a 512^3 grid, whose consecutive points are 2 MiB
-// apart, ran at under half the copy bandwidth.  Complex128: 2048 points and
-// 4 lines (64-byte pieces), two CTAs per SM.
-// Contiguous rows (x) of complex64 with N <= 512 use tiles of 4 rows at four
-// CTAs per SM and the swizzled shared layout: there each lane's points lie in
-// its own row, and fewer rows per warp request with longer pieces of each
-// (4 rows x 64 bytes rather than 8 x 32) measured faster.  Longer rows and
-// complex128 rows take the strided choice.
-template <typename R, int N, bool ROWS> __host__ __device__ constexpr bool rows_split()
+// Tile shapes.  Each pass kind has two compiled shapes, VAR 0 (the default)
+// and VAR 1; the plan autotuner times both on the plan's grid and keeps the
+// faster (the arithmetic per line is the same in both, so results are too).
+//
+// Strided lines (y, z).  complex64 VAR 0: tiles of at most 8192 points and 16
+// adjacent lines, so every point row of a tile is a 128-byte segment (one CTA
+// of <= 1024 threads per SM); with 8 lines (64-byte pieces) the z sweep of a
+// 512^3 grid, whose consecutive points are 2 MiB apart, ran at under half the
+// copy bandwidth.  VAR 1: 4096 points / 8 lines, two CTAs per SM.
+// complex128 VAR 0: 2048 points / 4 lines (64-byte pieces), two CTAs per SM;
+// VAR 1: 4096 points / 8 lines.
+// Contiguous rows (x).  A split tile holds half the points and lines (4 rows
+// of complex64 at four CTAs per SM) with the swizzled shared layout: each
+// lane's points lie in its own row, and fewer rows per warp request with
+// longer pieces of each (4 rows x 64 bytes rather than 8 x 32) measured faster
+// for complex64 rows of up to 512 points.  VAR 0 splits exactly those; VAR 1
+// takes the other choice for every row length of at least 8.
+template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr bool rows_split()
 {
-    return ROWS && sizeof(R) == 4 && N >= 8 && N <= 512;
+    constexpr bool dflt = sizeof(R) == 4 && N <= 512;
+    return ROWS && N >= 8 && (VAR == 0 ? dflt : !dflt);
 }
-template <typename R, int N, bool ROWS> __host__ __device__ constexpr int pick_lines()
+template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr int pick_lines()
 {
-    constexpr bool wide = !ROWS && sizeof(R) == 4;
-    constexpr int maxpts = sizeof(R) == 4 ? (wide ? 8192 : 4096) : 2048;
-    constexpr int lmax = rows_split<R, N, ROWS>() ? 4 : (sizeof(R) == 4 ? (wide ? 16 : 8) : 4);
-    constexpr int lmin = 1;
+    constexpr bool c64 = sizeof(R) == 4;
+    int maxpts = c64 ? 4096 : 2048, lmax = c64 ? 8 : 4;
+    if (ROWS) {
+        if (rows_split<R, N, ROWS, VAR>()) {
+            maxpts /= 2;
+            lmax /= 2;
+        }
+    } else if (c64 ? VAR == 0 : VAR == 1) {
+        maxpts *= 2;
+        lmax *= 2;
+    }
     int L = maxpts / N;
     if (L > lmax) L = lmax;
-    if (L < lmin) L = lmin;
+    if (L < 1) L = 1;
     return L;
 }
 // the on-chip 1D kernel keeps whole lines per thread group (row layout)
@@ -332,20 +346,36 @@ template <typename R> __host__ __device__ constexpr int lines_per_thread() { ret
 // shared by the thread's lines.  Tiles are software-pipelined: the points of
 // tile i+2 are copied into one of two shared buffers with cp.async while tile
 // i is transformed in the other.
-template <typename R, int N, int L, bool ROWS> constexpr int pass_min_blocks()
+template <typename R, int N, bool ROWS, int VAR>
+using PassTile = GTile<R, N, pick_lines<R, N, ROWS, VAR>(), lines_per_thread<R>(), rows_split<R, N, ROWS, VAR>()>;
+
+// dynamic shared memory of one CTA: two staging buffers, per-line reduction
+// scratch, twiddles, two mbarriers
+template <typename R, int N, bool ROWS, int VAR> constexpr size_t pass_smem_bytes()
 {
-    constexpr int nt = GTile<R, N, L, lines_per_thread<R>(), rows_split<R, N, ROWS>()>::NT;
+    using T = PassTile<R, N, ROWS, VAR>;
+    return 2 * sizeof(typename T::C) * T::SMEM_POINTS + sizeof(double) * (size_t)(T::SMEM_POINTS / T::E) +
+           sizeof(typename T::U) * N + 2 * sizeof(uint64_t);
+}
+// CTAs per SM the registers are budgeted for: 4 per SM for split rows (1024 /
+// threads per CTA, at most 16), else 2 (1 for CTAs of more than 512 threads),
+// never more than fit in the SM's shared memory
+template <typename R, int N, bool ROWS, int VAR> constexpr int pass_min_blocks()
+{
+    constexpr int nt = PassTile<R, N, ROWS, VAR>::NT;
     constexpr int want = 1024 / nt > 16 ? 16 : 1024 / nt;
-    return rows_split<R, N, ROWS>() && want > 2 ? want : (nt > 512 ? 1 : 2);
+    constexpr int b = rows_split<R, N, ROWS, VAR>() && want > 2 ? want : (nt > 512 ? 1 : 2);
+    constexpr int fit = (int)(227 * 1024 / (pass_smem_bytes<R, N, ROWS, VAR>() + 1024));
+    return b < fit ? b : (fit > 0 ? fit : 1);
 }
 
-template <typename R, int N, int L, bool ROWS>
-__global__ void __launch_bounds__(GTile<R, N, L, lines_per_thread<R>(), rows_split<R, N, ROWS>()>::NT,
-                                  (pass_min_blocks<R, N, L, ROWS>()))
+template <typename R, int N, bool ROWS, int VAR>
+__global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_blocks<R, N, ROWS, VAR>()))
     k_pass(const PassArgs a, const __grid_constant__ CUtensorMap tmap)
 {
     constexpr int LPT = lines_per_thread<R>();
-    using T = GTile<R, N, L, LPT, rows_split<R, N, ROWS>()>;
+    constexpr int L = pick_lines<R, N, ROWS, VAR>();
+    using T = PassTile<R, N, ROWS, VAR>;
     using C = typename T::C;
     using U = typename T::U;
     constexpr int E = T::E, TPL = T::TPL;
@@ -692,24 +722,23 @@ static cudaError_t prepare(K kern, LaunchCache &lc, int nt, size_t smem, int *ca
     return cudaSuccess;
 }
 
-template <typename R, int N, bool ROWS>
+template <typename R, int N, bool ROWS, int VAR>
 static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap)
 {
-    constexpr int L = pick_lines<R, N, ROWS>();
-    using T = GTile<R, N, L, lines_per_thread<R>(), rows_split<R, N, ROWS>()>;
+    constexpr int L = pick_lines<R, N, ROWS, VAR>();
+    using T = PassTile<R, N, ROWS, VAR>;
     static LaunchCache lc;
     static const CUtensorMap none = {};
-    const size_t smem = 2 * sizeof(typename T::C) * T::SMEM_POINTS + sizeof(double) * (N * L / T::E) +
-                        sizeof(typename T::U) * N + 2 * sizeof(uint64_t);
+    const size_t smem = pass_smem_bytes<R, N, ROWS, VAR>();
     if (a.tma_chunks > 0 && (ROWS || !tmap || (int64_t)a.tma_chunks * a.tma_box != N || a.tma_box > 256 ||
                              a.axis < 1 || a.o0n % L != 0))
         return cudaErrorInvalidValue;
     int cap = 0;
-    cudaError_t e = prepare(k_pass<R, N, L, ROWS>, lc, T::NT, smem, &cap);
+    cudaError_t e = prepare(k_pass<R, N, ROWS, VAR>, lc, T::NT, smem, &cap);
     if (e != cudaSuccess) return e;
     if (a.ntiles <= 0) return cudaSuccess;
     const int grid = (int)(a.ntiles < cap ? a.ntiles : cap);
-    k_pass<R, N, L, ROWS><<<grid, T::NT, smem, st>>>(a, tmap ? *tmap : none);
+    k_pass<R, N, ROWS, VAR><<<grid, T::NT, smem, st>>>(a, tmap ? *tmap : none);
     return cudaGetLastError();
 }
 
@@ -731,23 +760,25 @@ template <typename R, int N> static cudaError_t launch_line1d_t(const Line1DArgs
 
 #define GPE_FOR_EACH_N(X) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
 
-template <typename R, bool ROWS>
+template <typename R, bool ROWS, int VAR>
 static cudaError_t launch_pass_r(const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap)
 {
     switch (a.nax) {
 #define GPE_CASE(NN) \
-    case NN: return launch_pass_t<R, NN, ROWS>(a, st, tmap);
+    case NN: return launch_pass_t<R, NN, ROWS, VAR>(a, st, tmap);
         GPE_FOR_EACH_N(GPE_CASE)
 #undef GPE_CASE
     default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename R> static int lines_per_tile_r(bool rows, int n)
+template <typename R> static int lines_per_tile_r(bool rows, int n, int var)
 {
     switch (n) {
-#define GPE_CASE(NN) \
-    case NN: return rows ? pick_lines<R, NN, true>() : pick_lines<R, NN, false>();
+#define GPE_CASE(NN)                                                                                 \
+    case NN:                                                                                         \
+        return rows ? (var ? pick_lines<R, NN, true, 1>() : pick_lines<R, NN, true, 0>())            \
+                    : (var ? pick_lines<R, NN, false, 1>() : pick_lines<R, NN, false, 0>());
         GPE_FOR_EACH_N(GPE_CASE)
 #undef GPE_CASE
     default: return 0;

@@ -171,6 +171,9 @@ extern "C" gpe_status gpe_batch_create(const gpe_plan_desc *descs, int count, vo
             cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess)
             s = sfail(GPE_ECUDA, "stream creation failed");
         if (s == GPE_OK) s = gpe_plan_create(&d, g.st, &g.plan);
+        // tile shapes timed on this group's grid (per-thread staging: the group's
+        // instances are reached through a pointer array)
+        if (s == GPE_OK) s = gpe_plan_autotune(g.plan, nullptr, 3, GPE_TUNE_NO_TMA);
         if (s == GPE_OK) s = plan_prepare(g.plan);
         if (s == GPE_OK && (cudaMalloc((void **)&g.d_ptrs, sizeof(void *) * n) != cudaSuccess ||
                             cudaMalloc((void **)&g.d_slots, sizeof(int) * n) != cudaSuccess))

@@ -349,3 +349,50 @@ def test_copy_engine_staging_is_bit_identical(gpe, n, batch, prec):
         p.close()
     for a, b in zip(outs[0], outs[1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("n", [(64, 32, 16), (512, 8, 64), (16, 512), (1024, 64), (8, 64, 16)],
+                         ids=lambda n: "x".join(map(str, n)))
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_tile_shapes_and_autotuner_keep_results_bit_identical(gpe, n, prec):
+    """Every tile shape / staging combination gives the same bits; the autotuner
+    only reads the state it times on and picks one of the combinations."""
+    import torch
+    sp = _spec(n)
+    pv = gpe.GPE_C128 if prec == "c128" else gpe.GPE_C64
+    dt = np.complex128 if prec == "c128" else np.complex64
+    psi0 = gi.random_field(sp, seed=21, smooth=0.05).astype(dt)
+    combos = [{}, {gpe.GPE_OPT_TILE_X: 1}, {gpe.GPE_OPT_TILE_Y: 1, gpe.GPE_OPT_TILE_Z: 1},
+              {gpe.GPE_OPT_TILE_Y: 1, gpe.GPE_OPT_TILE_Z: 1, gpe.GPE_OPT_TMA_STAGING: 0},
+              {gpe.GPE_OPT_TILE_X: 1, gpe.GPE_OPT_TILE_Y: 1, gpe.GPE_OPT_TILE_Z: 1, gpe.GPE_OPT_TMA_Y: 0}]
+    outs = []
+    for opts in combos + ["tuned"]:
+        p = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma[: sp.ndim], prec=pv)
+        x = torch.from_numpy(psi0.copy()).cuda()
+        if opts == "tuned":
+            chosen = p.autotune(x, reps=2)
+            assert set(chosen.values()) <= {0, 1}
+            assert np.array_equal(x.cpu().numpy(), psi0)       # the tuner only read x
+        else:
+            for k, v in opts.items():
+                p.set_option(k, v)
+                assert p.get_option(k) == v
+        p.step_real(x, 3)
+        e = p.norm_energy(x)
+        torch.cuda.synchronize()
+        outs.append((x.cpu().numpy(), np.asarray(e)))
+        p.close()
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])
+
+
+def test_plan_options_reject_bad_values(gpe):
+    sp = _spec((32, 16))
+    p = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma[: sp.ndim], prec=gpe.GPE_C64)
+    for opt, val in ((gpe.GPE_OPT_TILE_X, 2), (gpe.GPE_OPT_TMA_STAGING, -1), (99, 0)):
+        with pytest.raises(gpe.GpeError) as ei:
+            p.set_option(opt, val)
+        assert ei.value.status == 1
+    with pytest.raises(gpe.GpeError):
+        gpe.gpe_plan_autotune(p._h, 0, 0, 0)
+    p.close()
