@@ -244,6 +244,26 @@ def taylor_green_3d(spec: Spec = CONFIG_3D_TG, seed=0, rho0=1.0, noise=0.01, kmo
 
 
 # ---------------------------------------------------------------- batched / serving
+def optical_lattice(spec: Spec, v0=5.0, periods=4, gamma=None):
+    """V = v0 sum_a sin^2(pi periods (x_a - lo_a) / L_a) (periodic on the box), plus an
+    optional harmonic confinement 1/2 sum gamma_a^2 x_a^2; grid-shaped float64 array."""
+    mesh = _mesh(spec)
+    v = np.zeros(spec.shape)
+    for a in range(spec.ndim):
+        v = v + v0 * np.sin(np.pi * periods * (mesh[a] - spec.lo[a]) / spec.length[a]) ** 2
+        if gamma is not None:
+            v = v + 0.5 * gamma[a] ** 2 * mesh[a] ** 2
+    return np.ascontiguousarray(v)
+
+
+def anharmonic(spec: Spec, gamma=(1.0, 1.0, 1.0), lam=0.05):
+    """V = 1/2 sum gamma_a^2 x_a^2 + lam (sum x_a^2)^2; grid-shaped float64 array."""
+    mesh = _mesh(spec)
+    r2 = sum(mesh[a] ** 2 for a in range(spec.ndim))
+    v = sum(0.5 * gamma[a] ** 2 * mesh[a] ** 2 for a in range(spec.ndim)) + lam * r2 ** 2
+    return np.ascontiguousarray(v)
+
+
 def batched_specs(count=512, seed=0, sizes=(64, 128, 256, 512), g_range=(0.0, 1000.0),
                   gamma_range=(1.0, 4.0), half_width=12.0, dt=1e-3, noise=0.01):
     """Uneven 2D instances: n uniform over `sizes` (square), box [-12,12)^2,

@@ -48,6 +48,7 @@ class _Grid(ctypes.Structure):
         ("g", ctypes.c_double),
         ("dt", ctypes.c_double),
         ("gamma", ctypes.c_double * 3),
+        ("V", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -150,10 +151,12 @@ class Problem:
     """Grid + physical parameters of one GPE instance.
 
     n: points per axis (x first); lo, length: box corner and size per axis;
-    g: interaction; dt: time step; gamma: trap frequencies, V = 1/2 sum g_a^2 x_a^2.
+    g: interaction; dt: time step; gamma: trap frequencies, V = 1/2 sum g_a^2 x_a^2;
+    V: optional potential sampled on the grid (array of the grid's shape, x
+    fastest), used instead of the harmonic one.
     """
 
-    def __init__(self, n, lo, length, g=0.0, dt=1e-3, gamma=None):
+    def __init__(self, n, lo, length, g=0.0, dt=1e-3, gamma=None, V=None):
         self.n = tuple(int(v) for v in n)
         self.lo = tuple(float(v) for v in lo)
         self.length = tuple(float(v) for v in length)
@@ -162,10 +165,16 @@ class Problem:
         self.gamma = tuple(float(v) for v in (gamma if gamma is not None else [0.0] * len(self.n)))
         self._g = _grid(self.n, self.lo, self.length, self.g, self.dt, self.gamma)
         self.N = int(np.prod(self.n))
+        self.V = None
+        if V is not None:
+            self.V = np.ascontiguousarray(V, dtype=np.float64).reshape(-1).copy()
+            if self.V.size != self.N:
+                raise ValueError("V has %d values, grid has %d" % (self.V.size, self.N))
+            self._g.V = self.V.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
     def replace(self, **kw):
         args = dict(n=self.n, lo=self.lo, length=self.length, g=self.g, dt=self.dt,
-                    gamma=self.gamma)
+                    gamma=self.gamma, V=self.V)
         args.update(kw)
         return Problem(**args)
 

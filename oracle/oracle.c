@@ -54,7 +54,9 @@ typedef struct {
     double len[3];     /* periodic box length */
     double g;          /* interaction parameter */
     double dt;         /* time step */
-    double gamma[3];   /* V = 1/2 sum_a gamma_a^2 x_a^2 */
+    double gamma[3];   /* V = 1/2 sum_a gamma_a^2 x_a^2 ... */
+    const double *V;   /* ... unless V != NULL: V sampled at every grid point
+                          (same order as psi); the model equation allows any V(r) */
 } orc_grid;
 
 static const double ORC_PI = 3.14159265358979323846264338327950288;
@@ -101,6 +103,7 @@ static void unflatten(const orc_grid *G, long idx, long j[3])
 /* harmonic trap V = 1/2 sum gamma_a^2 x_a^2 (paper, validation potentials) */
 static double potential(const orc_grid *G, const long j[3])
 {
+    if (G->V) return G->V[j[0] + G->n[0] * (j[1] + G->n[1] * j[2])];
     double v = 0.0;
     for (int a = 0; a < G->ndim; a++) {
         double x = coord(G, a, j[a]);

@@ -312,3 +312,63 @@ def test_vortex_field_is_periodic_and_winds_once_per_vortex():
             ang.append(th[j, i])
         wind = sum(wrap(ang[i + 1] - ang[i]) for i in range(len(ang) - 1)) / (2 * math.pi)
         assert round(wind) == qj
+
+
+# -------------------------------------------------------------- sampled potential
+# The model equation allows any potential V(r) (Eq. ndGPE); the oracle takes V
+# sampled at the grid points.  Pins: a constant potential only adds the global
+# phase exp(-i V0 t) in real time (every substep commutes with it), is removed
+# by the renormalisation in imaginary time, and shifts E and mu by V0 (norm 1).
+def _sp_v():
+    return gi.Spec(n=(32, 16, 8), lo=(-6.0, -5.0, -4.0), length=(12.0, 10.0, 8.0), g=40.0, dt=2e-3,
+                   gamma=(0.0, 0.0, 0.0))
+
+
+def test_constant_potential_is_a_global_phase(orc):
+    sp = _sp_v()
+    psi0 = gi.random_field(sp, seed=4, smooth=0.1)
+    v0, steps = 3.7, 25
+    ref = orc.Problem(**sp.kwargs()).step_real(psi0, steps)
+    out = orc.Problem(**sp.kwargs(), V=np.full(sp.shape, v0)).step_real(psi0, steps)
+    expect = ref * np.exp(-1j * v0 * steps * sp.dt)
+    assert np.max(np.abs(out - expect)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_constant_potential_drops_out_of_imaginary_time(orc):
+    """At g = 0 the factor exp(-V0 tau) commutes with every substep and the
+    renormalisation removes it.  (At g != 0 it would not: the second nonlinear
+    half-step sees |psi|^2 already scaled by the first.)"""
+    sp = gi.Spec(n=_sp_v().n, lo=_sp_v().lo, length=_sp_v().length, g=0.0, dt=2e-3, gamma=(0.0, 0.0, 0.0))
+    psi0 = gi.random_field(sp, seed=5, smooth=0.1)
+    v0 = 2.5
+    a = orc.Problem(**sp.kwargs()).step_imag(psi0, 12)
+    b = orc.Problem(**sp.kwargs(), V=np.full(sp.shape, v0)).step_imag(psi0, 12)
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_constant_potential_shifts_energy_and_mu(orc):
+    sp = _sp_v()
+    psi = gi.random_field(sp, seed=5, smooth=0.1)
+    v0 = 2.5
+    e0 = orc.Problem(**sp.kwargs()).norm_energy(psi)
+    e1 = orc.Problem(**sp.kwargs(), V=np.full(sp.shape, v0)).norm_energy(psi)
+    assert abs(e1[2] - (e0[2] + v0 * e0[0])) < 1e-11 * e0[0]
+    assert abs(e1[4] - (e0[4] + v0 * e0[0])) < 1e-11 * e0[0]
+    assert abs(e1[5] - (e0[5] + v0)) < 1e-11
+
+
+def test_sampled_potential_follows_the_grid_points(orc):
+    """V sampled at x_j = lo + j*L/n equals the built-in harmonic trap there, and
+    E_pot is the grid sum of V |psi|^2 dV."""
+    sp = gi.Spec(n=(16, 32, 8), lo=(-4.0, -6.0, -3.0), length=(8.0, 12.0, 6.0), g=10.0, dt=1e-3,
+                 gamma=(1.0, 1.5, 2.0))
+    psi0 = gi.random_field(sp, seed=6, smooth=0.1)
+    mesh = gi._mesh(sp)
+    V = sum(0.5 * sp.gamma[a] ** 2 * mesh[a] ** 2 for a in range(3))
+    a = orc.Problem(**sp.kwargs()).step_real(psi0, 9)
+    b = orc.Problem(**dict(sp.kwargs(), gamma=(0.0, 0.0, 0.0)), V=V).step_real(psi0, 9)
+    assert np.max(np.abs(a - b)) < 1e-12
+    lat = gi.optical_lattice(sp, v0=4.0, periods=2)
+    e = orc.Problem(**dict(sp.kwargs(), gamma=(0.0, 0.0, 0.0)), V=lat).norm_energy(psi0)
+    dv = np.prod([sp.length[i] / sp.n[i] for i in range(3)])
+    assert abs(e[2] - np.sum(lat * np.abs(psi0) ** 2) * dv) < 1e-12 * abs(e[2])
