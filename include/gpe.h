@@ -69,6 +69,12 @@ typedef struct gpe_plan_desc {
     int batch;                  /* instances stored back to back (>= 1)              */
     const double *g_each;       /* host, batch entries overriding g, or NULL         */
     const double *gamma_each;   /* host, batch*3 entries overriding gamma, or NULL   */
+    const double *V_host;       /* host, N values of a potential sampled at the grid
+                                   points (layout of one instance), shared by all
+                                   instances and used instead of the harmonic trap
+                                   (gamma and gamma_each must then be zero / NULL);
+                                   or NULL.  The model equation allows any V(r);
+                                   copied at plan creation.                         */
 } gpe_plan_desc;
 
 typedef struct gpe_plan gpe_plan;
@@ -141,6 +147,12 @@ gpe_status gpe_spectrum(gpe_plan *plan, const void *psi_dev, unsigned kinds, dou
  *   GPE_OPT_TILE_X/Y/Z   tile shape of the sweeps along x, y, z (0 default,
  *                        1 the alternative compiled shape: different lines per
  *                        tile and CTAs per SM).
+ *   GPE_OPT_TEST_STALL_COPIES  test hook for the failure handling: 1 makes
+ *                        every copy-engine tile wait expect 16 bytes more than
+ *                        its copies deliver, so the wait runs out after its
+ *                        limit (about 2 s per CTA), the pass abandons its
+ *                        tiles, and the next synchronising call returns
+ *                        GPE_ETIMEOUT.  Results of such a launch are undefined.
  * gpe_plan_set_option returns GPE_EINVAL for an unknown option or value and
  * takes effect at the next launch; gpe_plan_get_option reads one back. */
 enum gpe_option {
@@ -149,7 +161,8 @@ enum gpe_option {
     GPE_OPT_TILE_Y = 3,
     GPE_OPT_TILE_Z = 4,
     GPE_OPT_TMA_Y = 5,
-    GPE_OPT_TMA_Z = 6
+    GPE_OPT_TMA_Z = 6,
+    GPE_OPT_TEST_STALL_COPIES = 99
 };
 gpe_status gpe_plan_set_option(gpe_plan *plan, int option, int64_t value);
 gpe_status gpe_plan_get_option(const gpe_plan *plan, int option, int64_t *value);
@@ -189,7 +202,8 @@ gpe_status gpe_trace_read(gpe_plan *plan, int i, char *name, size_t name_len, in
  * fixed device array of about 2.4 MiB that every GPU loading the library
  * holds until the process exits; it calls no allocating routine.
  * Limit: N / n[a] <= GPE_NOALLOC_MAX_LINES on every axis (for example 1024^2,
- * 4096 x 32, 128^3); larger grids are rejected with GPE_EUNSUPPORTED.
+ * 4096 x 32, 128^3); larger grids, and descriptions with V_host, are rejected
+ * with GPE_EUNSUPPORTED.
  * The first call made on a device looks up the array's device address there
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call reuses the same array, so calls that overlap on the GPU (from

@@ -25,7 +25,8 @@ extern "C" {
 typedef struct gpe_batch gpe_batch;
 
 /* count instance descriptions (each with batch == 1 and no per-instance
- * arrays).  Instances are grouped; each group owns one plan, whose tile
+ * arrays; V_host is rejected with GPE_EUNSUPPORTED, here and by
+ * gpe_serve_submit).  Instances are grouped; each group owns one plan, whose tile
  * shapes are chosen by gpe_plan_autotune on the group's grid (per-thread
  * staging; one scratch array of the group's size while the call runs).  The
  * batch enqueues on cuda_stream (NULL: legacy default stream). */

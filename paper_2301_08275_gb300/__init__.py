@@ -54,6 +54,7 @@ class gpe_plan_desc(ctypes.Structure):
         ("batch", ctypes.c_int),
         ("g_each", ctypes.POINTER(ctypes.c_double)),
         ("gamma_each", ctypes.POINTER(ctypes.c_double)),
+        ("V_host", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -209,6 +210,7 @@ def gpe_norm_energy_noalloc(desc, psi_ptr, stream=None):
 
 
 GPE_OPT_TMA_STAGING, GPE_OPT_TILE_X, GPE_OPT_TILE_Y, GPE_OPT_TILE_Z, GPE_OPT_TMA_Y, GPE_OPT_TMA_Z = 1, 2, 3, 4, 5, 6
+GPE_OPT_TEST_STALL_COPIES = 99
 GPE_TUNE_NO_TMA = 1
 
 
@@ -248,7 +250,7 @@ def gpe_trace_read(plan, i):
 
 # ------------------------------------------------------------- torch-facing plan
 def make_desc(n, lo, length, g=0.0, dt=1e-3, gamma=None, prec=GPE_C64, batch=1, g_each=None,
-              gamma_each=None):
+              gamma_each=None, V=None):
     d = gpe_plan_desc()
     nd = len(n)
     d.ndim = nd
@@ -270,6 +272,10 @@ def make_desc(n, lo, length, g=0.0, dt=1e-3, gamma=None, prec=GPE_C64, batch=1, 
         gm = np.ascontiguousarray(gamma_each, dtype=np.float64).reshape(-1)
         keep.append(gm)
         d.gamma_each = _dptr(gm)
+    if V is not None:
+        vv = np.ascontiguousarray(V, dtype=np.float64).reshape(-1)
+        keep.append(vv)
+        d.V_host = _dptr(vv)
     return d, keep
 
 
@@ -281,7 +287,7 @@ class Plan:
     """
 
     def __init__(self, n, lo, length, g=0.0, dt=1e-3, gamma=None, prec=GPE_C64, batch=1, g_each=None,
-                 gamma_each=None, stream=None):
+                 gamma_each=None, stream=None, V=None):
         import torch
         self.n = tuple(int(v) for v in n)
         self.batch = int(batch)
@@ -290,7 +296,7 @@ class Plan:
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        desc, keep = make_desc(n, lo, length, g, dt, gamma, prec, batch, g_each, gamma_each)
+        desc, keep = make_desc(n, lo, length, g, dt, gamma, prec, batch, g_each, gamma_each, V)
         self._h = gpe_plan_create(desc, stream.cuda_stream)
         del keep
 

@@ -86,6 +86,7 @@ struct gpe_plan {
     int device = 0;
     bool trap[3] = {false, false, false};
     void *tw[3] = {}, *kt[3] = {}, *ki[3] = {}, *vh[3] = {}, *vf[3] = {}, *vi[3] = {};
+    void *vsamp = nullptr;       // sampled potential [N] in the bulk real type, or NULL
     double *g_dev = nullptr, *gamma_dev = nullptr, *scale = nullptr, *partials = nullptr;
     double *sums = nullptr, *out6 = nullptr, *out4 = nullptr;
     int *err = nullptr;
@@ -118,6 +119,7 @@ struct gpe_plan {
     Tmap tmaps[3];
     bool use_tma[3] = {true, true, true};   // copy-engine staging per axis (strided axes only)
     int tile_var[3] = {0, 0, 0};            // tile shape per axis
+    int tx_extra = 0;                       // GPE_OPT_TEST_STALL_COPIES
 };
 
 static gpe_status check_err(gpe_plan *p);
@@ -272,6 +274,15 @@ extern "C" gpe_status gpe_plan_create(const gpe_plan_desc *d, void *cuda_stream,
     for (int a = 0; a < d->ndim; ++a) p->dv *= p->h[a];
 
     const int64_t B = p->batch;
+    if (d->V_host) {
+        bool ok = !d->gamma_each;
+        for (int a = 0; a < d->ndim; ++a) ok = ok && d->gamma[a] == 0.0;
+        for (int64_t i = 0; ok && i < p->N; ++i) ok = isfinite(d->V_host[i]);
+        if (!ok) {
+            destroy(p);
+            return fail(GPE_EINVAL, "V_host needs finite values and gamma = 0, gamma_each = NULL");
+        }
+    }
     std::vector<double> gs(B), gam(3 * B, 0.0);
     for (int64_t b = 0; b < B; ++b) {
         gs[b] = d->g_each ? d->g_each[b] : d->g;
@@ -320,6 +331,28 @@ extern "C" gpe_status gpe_plan_create(const gpe_plan_desc *d, void *cuda_stream,
             PLAN_TRY(upload_cplx(p, &p->vh[a], vh));
             PLAN_TRY(upload_cplx(p, &p->vf[a], vf));
             PLAN_TRY(upload_real(p, &p->vi[a], vi));
+        }
+    }
+    if (d->V_host) {
+        // the sampled values, and for 1D the same potential as trap tables of
+        // the on-chip kernel (exact: in 1D a sampled V is a per-axis table)
+        PLAN_TRY(upload_real(p, &p->vsamp, std::vector<double>(d->V_host, d->V_host + p->N)));
+        if (d->ndim == 1) {
+            const int64_t na = p->n[0];
+            std::vector<double> vh(2 * na * B), vf(2 * na * B), vi(na * B);
+            for (int64_t b = 0; b < B; ++b)
+                for (int64_t j = 0; j < na; ++j) {
+                    const double th = d->V_host[j] * p->dt;
+                    vh[2 * (b * na + j)] = -2.0 * sin(0.25 * th) * sin(0.25 * th);
+                    vh[2 * (b * na + j) + 1] = -sin(0.5 * th);
+                    vf[2 * (b * na + j)] = -2.0 * sin(0.5 * th) * sin(0.5 * th);
+                    vf[2 * (b * na + j) + 1] = -sin(th);
+                    vi[b * na + j] = exp(-0.5 * th);
+                }
+            PLAN_TRY(upload_cplx(p, &p->vh[0], vh));
+            PLAN_TRY(upload_cplx(p, &p->vf[0], vf));
+            PLAN_TRY(upload_real(p, &p->vi[0], vi));
+            p->trap[0] = true;
         }
     }
     // per-instance parameters and reduction buffers (always double precision)
@@ -533,6 +566,8 @@ static PassArgs make_pass(const gpe_plan *p, int axis, const void *src, void *ds
     a.vi_ax = p->vi[axis];
     a.vi_o0 = h0 ? p->vi[o0] : nullptr;
     a.vi_o1 = h1 ? p->vi[o1] : nullptr;
+    a.vsamp = p->ndim >= 2 ? p->vsamp : nullptr;
+    a.vsamp_diag = p->vsamp;
     a.g = p->g_dev;
     a.inv_n = 1.0 / (double)p->N;
     a.scale = p->scale;
@@ -634,6 +669,7 @@ static gpe_status run(gpe_plan *p, const PassArgs &a_in)
                 tm = &c.map;
                 a.tma_box = box;
                 a.tma_chunks = a.nax / box;
+                a.tx_extra = p->tx_extra;
             }
         }
     }
@@ -776,6 +812,10 @@ extern "C" gpe_status gpe_plan_set_option(gpe_plan *p, int option, int64_t value
 {
     if (!p) return fail(GPE_EINVAL, "NULL plan");
     if (value != 0 && value != 1) return fail(GPE_EINVAL, "plan options take 0 or 1");
+    if (option == GPE_OPT_TEST_STALL_COPIES) {
+        p->tx_extra = value ? 16 : 0;
+        return GPE_OK;
+    }
     if (option == GPE_OPT_TMA_STAGING) {
         for (int a = 0; a < 3; ++a) p->use_tma[a] = value != 0;
         return GPE_OK;
@@ -797,6 +837,7 @@ extern "C" gpe_status gpe_plan_get_option(const gpe_plan *p, int option, int64_t
     if (option == GPE_OPT_TMA_STAGING) *value = (p->use_tma[1] || p->use_tma[2]) ? 1 : 0;
     else if (option >= GPE_OPT_TILE_X && option <= GPE_OPT_TILE_Z) *value = p->tile_var[option - GPE_OPT_TILE_X];
     else if (option == GPE_OPT_TMA_Y || option == GPE_OPT_TMA_Z) *value = p->use_tma[option - GPE_OPT_TMA_Y + 1] ? 1 : 0;
+    else if (option == GPE_OPT_TEST_STALL_COPIES) *value = p->tx_extra ? 1 : 0;
     else return fail(GPE_EINVAL, "unknown plan option");
     return GPE_OK;
 }

@@ -51,6 +51,11 @@ struct PassArgs {
     // kinetic tables ([n]); NULL when absent (1D/2D other axes)
     const void *kt_ax, *kt_o0, *kt_o1;   // offsets exp(-i k_a^2 dt/2) - 1
     const void *ki_ax, *ki_o0, *ki_o1;   // real
+    // potential sampled at the grid points ([N] of one instance, shared by all;
+    // real type of the bulk precision), or NULL: vsamp enters the nonlinear
+    // substeps, vsamp_diag the potential energy (both set for 2D/3D; 1D steps
+    // take the same values through the trap tables, so only vsamp_diag is set)
+    const void *vsamp, *vsamp_diag;
     const double *g;       // per-instance interaction
     double nl_c;           // theta = g * nl_c * |psi|^2
     double inv_n;          // 1/N applied with the kinetic substep
@@ -69,6 +74,8 @@ struct PassArgs {
     // tma_chunks > 0 each tile is fetched as tma_chunks boxes of tma_box points
     // along the axis through the tensor map passed beside these arguments
     int tma_chunks, tma_box;
+    int tx_extra;          // bytes added to each tile's expected count (0; > 0 only in the
+                           // failure-handling test, so that the wait runs out)
     int *err;              // device error word (bit ERR_TMA_TIMEOUT), may be NULL
 };
 

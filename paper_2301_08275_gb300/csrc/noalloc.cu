@@ -155,6 +155,7 @@ extern "C" gpe_status gpe_norm_energy_noalloc(const gpe_plan_desc *d, const void
     if (d->ndim < 1 || d->ndim > 3) return nfail(GPE_EUNSUPPORTED, "ndim must be 1, 2 or 3");
     if (d->prec != GPE_C64 && d->prec != GPE_C128) return nfail(GPE_EINVAL, "prec must be GPE_C64 or GPE_C128");
     if (d->batch != 1) return nfail(GPE_EINVAL, "gpe_norm_energy_noalloc handles one instance (batch must be 1)");
+    if (d->V_host) return nfail(GPE_EUNSUPPORTED, "gpe_norm_energy_noalloc takes the harmonic trap only");
     int64_t n[3] = {1, 1, 1}, N = 1;
     double lo[3] = {0, 0, 0}, h[3] = {0, 0, 0}, kf[3] = {0, 0, 0}, dv = 1.0;
     for (int a = 0; a < d->ndim; ++a) {

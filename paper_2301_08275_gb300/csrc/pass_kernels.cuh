@@ -124,9 +124,10 @@ __device__ __forceinline__ double line_sum(double x, double *red, int l, int tl)
 // pointwise substep on the E points (indices tl + TPL*e on this axis) of one line
 // inst: position of the instance in this launch (renormalisation factor);
 // ti: its parameter/table slot
+// off: offset of the line's first point within its instance (sampled potential)
 template <typename R, int E, int TPL>
 __device__ __forceinline__ void point_op(int op, typename CT<R>::C (&v)[E], const PassArgs &a, int inst,
-                                         int ti, int c0, int c1, int tl)
+                                         int ti, int c0, int c1, int tl, int64_t off)
 {
     using C = typename CT<R>::C;
     if (op == OP_NONE) return;
@@ -172,9 +173,12 @@ __device__ __forceinline__ void point_op(int op, typename CT<R>::C (&v)[E], cons
         const U f1 = v1 ? v1[(int64_t)ti * a.o1n + c1] : U{};
         R th[E];
         R mx = (R)0;
+        const R *vs = static_cast<const R *>(a.vsamp);
+        const R cc = (R)a.nl_c;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             th[e] = gc * cabs2(v[e]);
+            if (vs) th[e] = fma(vs[off + (int64_t)(tl + TPL * e) * a.estride], cc, th[e]);
             mx = fmax(mx, fabs(th[e]));
         }
         // the whole warp takes the short series when all its angles are small
@@ -206,9 +210,13 @@ __device__ __forceinline__ void point_op(int op, typename CT<R>::C (&v)[E], cons
     R fl = (R)1;
     if (a.vi_o0) fl *= static_cast<const R *>(a.vi_o0)[(int64_t)ti * a.o0n + c0];
     if (a.vi_o1) fl *= static_cast<const R *>(a.vi_o1)[(int64_t)ti * a.o1n + c1];
+    const R *vs = static_cast<const R *>(a.vsamp);
+    const R cc = (R)a.nl_c;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        R f = fl * exp_r(-gc * cabs2(v[e]));
+        R th = gc * cabs2(v[e]);
+        if (vs) th = fma(vs[off + (int64_t)(tl + TPL * e) * a.estride], cc, th);
+        R f = fl * exp_r(-th);
         if (iax) f *= iax[(int64_t)ti * a.nax + tl + TPL * e];
         v[e] = cscale(v[e], f);
     }
@@ -413,7 +421,7 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
                 const int c0 = int(li & (a.o0n - 1)), c1 = int(li >> a.lg_o0);
                 const int x = c0 * (int)(sizeof(C) / 8);      // complex128 rows are pairs of doubles
                 fence_async_shared();
-                mbar_expect_tx(&mbar[b], (unsigned)(sizeof(C) * N * L));
+                mbar_expect_tx(&mbar[b], (unsigned)(sizeof(C) * N * L) + (unsigned)a.tx_extra);
                 for (int c = 0; c < a.tma_chunks; ++c) {
                     const int pa = c * a.tma_box;
                     if (a.axis == 1) tma_load_4d(buf + pa * L, &tmap, x, pa, c1, inst, &mbar[b]);
@@ -471,10 +479,11 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
         if (a.red == RED_DIAG_X) {
             // real-space moments of rho = |psi|^2 along each row, then kx^2 |F_x psi|^2
             const R lox = (R)a.lo[0], hx = (R)a.h[0];
-            R s0[LPT], sx2[LPT], s4[LPT];
+            const R *vsd = static_cast<const R *>(a.vsamp_diag);
+            R s0[LPT], sx2[LPT], s4[LPT], sv[LPT];
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln) {
-                s0[ln] = sx2[ln] = s4[ln] = (R)0;
+                s0[ln] = sx2[ln] = s4[ln] = sv[ln] = (R)0;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const R x = lox + (R)(tl + TPL * e) * hx;
@@ -482,6 +491,7 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
                     s0[ln] += rho;
                     sx2[ln] += x * x * rho;
                     s4[ln] += rho * rho;
+                    if (vsd) sv[ln] += vsd[g[ln].off + (int64_t)(tl + TPL * e) * a.estride] * rho;
                 }
             }
             T::template fft<-1>(v, sm, tl, l0, tw);
@@ -508,7 +518,7 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
                 q[1][ln] = (double)sx2[ln];
                 q[2][ln] = y * y * (double)s0[ln];
                 q[3][ln] = z * z * (double)s0[ln];
-                q[4][ln] = 0.5 * gx * gx * (double)sx2[ln] + vyz * (double)s0[ln];
+                q[4][ln] = 0.5 * gx * gx * (double)sx2[ln] + vyz * (double)s0[ln] + (double)sv[ln];
                 q[5][ln] = (double)s4[ln];
                 q[6][ln] = (double)sk[ln];
             }
@@ -541,17 +551,17 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
         } else {
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln)
-                point_op<R, E, TPL>(a.op_pre, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl);
+                point_op<R, E, TPL>(a.op_pre, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
             if (a.fft1 < 0) T::template fft<-1>(v, sm, tl, l0, tw);
             else if (a.fft1 > 0) T::template fft<1>(v, sm, tl, l0, tw);
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln)
-                point_op<R, E, TPL>(a.op_mid, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl);
+                point_op<R, E, TPL>(a.op_mid, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
             if (a.fft2 < 0) T::template fft<-1>(v, sm, tl, l0, tw);
             else if (a.fft2 > 0) T::template fft<1>(v, sm, tl, l0, tw);
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln)
-                point_op<R, E, TPL>(a.op_post, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl);
+                point_op<R, E, TPL>(a.op_post, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
             if (a.red == RED_NORM) {
                 double sn[LPT];
 #pragma unroll

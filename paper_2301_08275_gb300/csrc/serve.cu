@@ -78,6 +78,7 @@ gpe_status check_desc(const gpe_plan_desc &d)
 {
     if (d.batch != 1) return sfail(GPE_EINVAL, "each instance description must have batch == 1");
     if (d.g_each || d.gamma_each) return sfail(GPE_EINVAL, "per-instance arrays are not used here");
+    if (d.V_host) return sfail(GPE_EUNSUPPORTED, "sampled potentials are taken by single plans only");
     return GPE_OK;
 }
 

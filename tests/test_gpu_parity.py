@@ -389,7 +389,7 @@ def test_tile_shapes_and_autotuner_keep_results_bit_identical(gpe, n, prec):
 def test_plan_options_reject_bad_values(gpe):
     sp = _spec((32, 16))
     p = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma[: sp.ndim], prec=gpe.GPE_C64)
-    for opt, val in ((gpe.GPE_OPT_TILE_X, 2), (gpe.GPE_OPT_TMA_STAGING, -1), (99, 0)):
+    for opt, val in ((gpe.GPE_OPT_TILE_X, 2), (gpe.GPE_OPT_TMA_STAGING, -1), (98, 0)):
         with pytest.raises(gpe.GpeError) as ei:
             p.set_option(opt, val)
         assert ei.value.status == 1

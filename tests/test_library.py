@@ -56,11 +56,11 @@ def test_desc_layout_matches_header():
 #include <stddef.h>
 #include "gpe.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(gpe_plan_desc),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(gpe_plan_desc),
     offsetof(gpe_plan_desc, ndim), offsetof(gpe_plan_desc, n), offsetof(gpe_plan_desc, lo),
     offsetof(gpe_plan_desc, len), offsetof(gpe_plan_desc, g), offsetof(gpe_plan_desc, dt),
     offsetof(gpe_plan_desc, gamma), offsetof(gpe_plan_desc, prec), offsetof(gpe_plan_desc, batch),
-    offsetof(gpe_plan_desc, g_each), offsetof(gpe_plan_desc, gamma_each));
+    offsetof(gpe_plan_desc, g_each), offsetof(gpe_plan_desc, gamma_each), offsetof(gpe_plan_desc, V_host));
   return 0; }
 '''
     d = "/tmp/gpe_desc_check_%d" % os.getpid()
@@ -73,7 +73,7 @@ int main(void) {
     D = gpe.gpe_plan_desc
     py = [ctypes.sizeof(D)] + [getattr(D, f).offset for f in
                                ("ndim", "n", "lo", "len", "g", "dt", "gamma", "prec", "batch", "g_each",
-                                "gamma_each")]
+                                "gamma_each", "V_host")]
     assert vals == py
 
 
