@@ -34,9 +34,12 @@ WORKLOADS = {
     "tg512": dict(spec=gi.CONFIG_3D_TG, prec="c64",
                   name="3D Taylor-Green 512^3, complex64 bulk / FP64 tables and reductions, real time, "
                        "dt=1e-3, V=0, g=1, box side 2*pi*16"),
-    "turb1024": dict(spec=gi.CONFIG_2D, prec="c64",
+    "turb1024": dict(spec=gi.CONFIG_2D, prec="c64", spectra_every=200,
                      name="2D quantum turbulence 1024^2, complex64, real time, dt=5e-4, V=0, g=1, "
-                          "512 vortices, box side 2*pi*32"),
+                          "512 vortices, box side 2*pi*32; incompressible/compressible spectra every 200 steps"),
+    "turb1024c128": dict(spec=gi.CONFIG_2D, prec="c128", spectra_every=200,
+                         name="2D quantum turbulence 1024^2, complex128, real time, dt=5e-4, V=0, g=1, "
+                              "512 vortices, box side 2*pi*32; incompressible/compressible spectra every 200 steps"),
     "line256": dict(spec=gi.CONFIG_1D, prec="c128",
                     name="1D 256 points complex128, real time, dt=1e-3, V=x^2/2, g=10"),
 }
@@ -49,7 +52,7 @@ KERNEL_SOURCES = ["fft_tile.cuh", "pass_kernels.cuh", "pass_f32.cu", "pass_f32_s
 def initial_state(key, spec, seed=0):
     if key == "tg512":
         return gi.taylor_green_3d(spec, seed=seed)
-    if key == "turb1024":
+    if key.startswith("turb1024"):
         return gi.vortex_field_2d(spec, nv=512, seed=seed)[0]
     return gi.gaussian_1d(spec, seed=seed)
 
@@ -306,7 +309,14 @@ def run_ours(args, key, wl):
     with ClockSampler(local) as clk:
         barrier()
         ev0.record(stream)
-        plan.step_real(psi, args.steps)
+        if wl.get("spectra_every"):
+            # turbulence runs read the kinetic-energy spectra back every few hundred steps
+            se = wl["spectra_every"]
+            for s0 in range(0, args.steps, se):
+                plan.step_real(psi, min(se, args.steps - s0))
+                plan.spectrum(psi)
+        else:
+            plan.step_real(psi, args.steps)
         ev1.record(stream)
         barrier()
     ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
@@ -511,13 +521,140 @@ def run_serving(args):
     return 0
 
 
+def run_trap(args):
+    """3D anisotropic trap 256^3, gamma = (1, 2, 4), g = 200, box [-8, 8)^3, complex64:
+    the ground state by imaginary time (renormalised every step) until |dE| < 1e-10
+    between checks every 16 steps, then the trap frequencies doubled and
+    `--steps` real-time steps with the rms sizes read back every 10 steps.
+    value = grid-point updates/s of the real-time phase including the rms
+    reads; the imaginary-time phase is reported beside it."""
+    import torch
+    import paper_2301_08275_gb300 as gpe
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gpe.build()
+    sp = gi.CONFIG_3D_TRAP
+    if args.grid:
+        sp = gi.Spec(n=tuple(int(v) for v in args.grid.split(",")), lo=sp.lo, length=sp.length, g=sp.g,
+                     dt=sp.dt, gamma=sp.gamma)
+    quench = tuple(2.0 * g for g in sp.gamma)
+    stream = torch.cuda.Stream(device=dev)
+    pi = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma, prec=gpe.GPE_C64, stream=stream)
+    pr = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=quench, prec=gpe.GPE_C64, stream=stream)
+    psi = torch.from_numpy(gi.harmonic_gaussian(sp, seed=rank, noise=0.01).astype(np.complex64)).to(dev)
+    torch.cuda.synchronize(dev)
+    tiles_i = pi.autotune(psi, reps=3)
+    tiles_r = pr.autotune(psi, reps=3)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # warm-up on copies (the timed phases start from the real initial state)
+    w = psi.clone()
+    pi.step_imag(w, max(3, args.warmup), etol=0.0, check_every=max(3, args.warmup))
+    pr.step_real(w, max(3, args.warmup))
+    pr.rms_size(w)
+    del w
+    barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    done, e_ground = pi.step_imag(psi, args.imag_max, target_norm=1.0, etol=1e-10, check_every=16)
+    ev[1].record(stream)
+    barrier()
+    ms_imag = max_over_ranks(ev[0].elapsed_time(ev[1]), dev)
+    ground = pi.norm_energy(psi)[0]
+    sig0 = pi.rms_size(psi)[0]
+    sig = []
+    with ClockSampler(local) as clk:
+        barrier()
+        ev[2].record(stream)
+        for s0 in range(0, args.steps, 10):
+            pr.step_real(psi, min(10, args.steps - s0))
+            sig.append(pr.rms_size(psi)[0])
+        ev[3].record(stream)
+        barrier()
+    ms_real = max_over_ranks(ev[2].elapsed_time(ev[3]), dev)
+    value = ws * sp.N * args.steps / (ms_real / 1e3)
+    # per-kernel timing of the real-time step, traced
+    pr.trace(True)
+    barrier()
+    pr.step_real(psi, 100)
+    barrier()
+    tr = pr.trace_read()
+    pr.trace(False)
+    kind, (cnt, tot) = max(tr.items(), key=lambda kv: kv[1][1])
+    avg_ms = tot / cnt
+    bpl = 2.0 * sp.N * 8
+    peak, peak_src = measured_peaks()
+    achieved = bpl / (avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": kind, "kernel_avg_ms": avg_ms, "bytes_per_launch": bpl,
+                "peak_source": peak_src,
+                "kernels": {k: {"launches": c, "avg_ms": t / c} for k, (c, t) in tr.items()}}
+    # end to end: host buffer in and out every step
+    e2e_steps = 10
+    host = torch.empty(psi.shape, dtype=torch.complex64, pin_memory=True)
+    host.copy_(psi.cpu())
+    hnp = host.numpy()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        pr.step_real_host(hnp, 1)
+    el = max_over_ranks(time.perf_counter() - t0, dev)
+    state_bytes = sp.N * 8
+    e2e = {"value": ws * sp.N * e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+           "d2h_bytes_per_step": state_bytes, "steps": e2e_steps,
+           "api": "gpe_step_real_host (1 step per call, pinned host buffer)"}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        cores = oracle.set_threads(0)
+        P = oracle.Problem(**dict(sp.kwargs(), gamma=quench))
+        x = psi.cpu().numpy().astype(np.complex128)
+        n, t0 = 0, time.perf_counter()
+        while True:
+            x = P.step_real(x, 1)
+            n += 1
+            t = time.perf_counter() - t0
+            if t > 20.0 or t * (n + 1) / n > 24.0:
+                break
+        cpu = {"value": sp.N * n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d real-time step(s) of the quenched 256^3 trap on the FP64 oracle, %.1f s" % (n, t)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_real / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "3D trap %s, gamma=(1,2,4) -> (2,4,8) after the ground state, g=200, "
+                                       "box [-8,8)^3, dt=1e-3, complex64 bulk / FP64 tables and reductions; "
+                                       "rms sizes read back every 10 real-time steps" % "x".join(map(str, sp.n)),
+                           "grid": list(sp.n), "l2": "state %.2f GiB > L2: no flush" % (state_bytes / 2 ** 30),
+                           "tiles_imag": tiles_i, "tiles_real": tiles_r},
+                "imag": {"steps_to_converge": int(done), "ms_per_step": ms_imag / max(1, done),
+                         "updates_per_s": ws * sp.N * done / (ms_imag / 1e3), "E": float(e_ground[0]),
+                         "mu": float(ground[5]), "sigma": [float(v) for v in sig0[:3]], "r_rms": float(sig0[3])},
+                "sigma_final": [float(v) for v in sig[-1][:3]] if sig else None,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+                "gpu_launches": int(sum(c for c, _ in tr.values()))}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tg512", choices=sorted(WORKLOADS) + ["batched", "serving"])
+    ap.add_argument("--workload", default="tg512", choices=sorted(WORKLOADS) + ["batched", "serving", "trap256"])
+    ap.add_argument("--imag-max", type=int, default=20000, help="trap256: imaginary-time step limit")
     ap.add_argument("--instances", type=int, default=512, help="batched: number of instances")
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
     ap.add_argument("--max-active", type=int, default=32, help="serving: resident requests")
@@ -533,6 +670,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "trap256":
+        return run_trap(args)
     wl = dict(WORKLOADS[args.workload])
     if args.grid:
         sp = wl["spec"]
