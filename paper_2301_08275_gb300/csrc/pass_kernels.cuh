@@ -30,8 +30,25 @@ __device__ __forceinline__ double2 phase_offset(double th)
     sincos(0.5 * th, &s, &c);
     return mk(-2.0 * s * s, -2.0 * s * c);
 }
-// short form for |th| <= 1/16: truncation below 1e-12 (sin) and 1e-14 (cos),
+// short forms for |th| <= 1/16 (Maclaurin series of cos th - 1 and sin th).
+// double: terms to th^12 / th^13, truncation below 1e-27;
+// float: terms to th^6 / th^5, truncation below 1e-12 (sin) and 1e-14 (cos),
 // so the modulus of 1 + w stays one to about 1e-13
+__device__ __forceinline__ double2 phase_offset_small(double th)
+{
+    const double u = th * th;
+    const double cm =
+        u * fma(u, fma(u, fma(u, fma(u, fma(u, 1.0 / 479001600.0, -1.0 / 3628800.0), 1.0 / 40320.0), -1.0 / 720.0),
+                       1.0 / 24.0),
+                -0.5);
+    const double sn =
+        th * fma(u, fma(u, fma(u, fma(u, fma(u, fma(u, 1.0 / 6227020800.0, -1.0 / 39916800.0), 1.0 / 362880.0),
+                                         -1.0 / 5040.0),
+                                 1.0 / 120.0),
+                         -1.0 / 6.0),
+                 1.0);
+    return mk(cm, -sn);
+}
 __device__ __forceinline__ float2 phase_offset_small(float th)
 {
     const float u = th * th;
@@ -52,6 +69,24 @@ __device__ __forceinline__ float2 phase_offset(float th)
     float s, c;
     sincosf(0.5f * th, &s, &c);
     return mk(-2.0f * s * s, -2.0f * s * c);
+}
+
+// v_e <- v_e (1 + w_e), w_e = exp(-i th_e) - 1, for the E angles a thread
+// holds: the short series when every angle of the warp is at most 1/16 (the
+// usual case: dt |V + g|psi|^2| is far below it), else the long form
+template <typename C, typename R, int E>
+__device__ __forceinline__ void apply_phase(C (&v)[E], const R (&th)[E])
+{
+    R mx = (R)0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) mx = fmax(mx, fabs(th[e]));
+    if (__all_sync(__activemask(), mx <= (R)0.0625)) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = cmadd1(v[e], phase_offset_small(th[e]));
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = cmadd1(v[e], phase_offset(th[e]));
+    }
 }
 
 // Tile shapes.  Each pass kind has two compiled shapes, VAR 0 (the default)
@@ -135,10 +170,10 @@ __device__ __forceinline__ void point_op(int op, typename CT<R>::C (&v)[E], cons
     if (op == OP_KREAL) {
         // tables hold exp(-i k_a^2 dt/2) - 1; the 1/N of the inverse transform is exact
         const U *kt = static_cast<const U *>(a.kt_ax);
+        const R invn = (R)a.inv_n;
         const U *k0 = static_cast<const U *>(a.kt_o0);
         const U *k1 = static_cast<const U *>(a.kt_o1);
         const U f0 = k0 ? k0[c0] : U{}, f1 = k1 ? k1[c1] : U{};
-        const R invn = (R)a.inv_n;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             C x = uomul(v[e], kt[tl + TPL * e]);
@@ -171,29 +206,19 @@ __device__ __forceinline__ void point_op(int op, typename CT<R>::C (&v)[E], cons
         const U *v1 = static_cast<const U *>(a.vt_o1);
         const U f0 = v0 ? v0[(int64_t)ti * a.o0n + c0] : U{};
         const U f1 = v1 ? v1[(int64_t)ti * a.o1n + c1] : U{};
+        // separate paths with and without a sampled potential keep the
+        // common one free of its address arithmetic (fewer live registers)
         R th[E];
-        R mx = (R)0;
-        const R *vs = static_cast<const R *>(a.vsamp);
-        const R cc = (R)a.nl_c;
+        if (a.vsamp) {
+            const R *vs = static_cast<const R *>(a.vsamp) + off;
+            const R cc = (R)a.nl_c;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            th[e] = gc * cabs2(v[e]);
-            if (vs) th[e] = fma(vs[off + (int64_t)(tl + TPL * e) * a.estride], cc, th[e]);
-            mx = fmax(mx, fabs(th[e]));
-        }
-        // the whole warp takes the short series when all its angles are small
-        // (the usual case: dt |V + g|psi|^2| is far below 1/16)
-        bool small = false;
-        if constexpr (sizeof(R) == 4) {
-            small = __all_sync(__activemask(), mx <= 0.0625f);
-            if (small) {
+            for (int e = 0; e < E; ++e) th[e] = fma(vs[(int64_t)(tl + TPL * e) * a.estride], cc, gc * cabs2(v[e]));
+            apply_phase<C, R, E>(v, th);
+        } else {
 #pragma unroll
-                for (int e = 0; e < E; ++e) v[e] = cmadd1(v[e], phase_offset_small(th[e]));
-            }
-        }
-        if (!small) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) v[e] = cmadd1(v[e], phase_offset(th[e]));
+            for (int e = 0; e < E; ++e) th[e] = gc * cabs2(v[e]);
+            apply_phase<C, R, E>(v, th);
         }
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -602,6 +627,8 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
 }
 
 // ------------------------------------------------------------------ 1D on chip
+__host__ __device__ constexpr size_t line1d_red_bytes(int nt) { return (sizeof(double) * (size_t)nt + 15) / 16 * 16; }
+
 // Each line is one instance and stays in registers for all nsteps steps of
 // the launch; real time merges consecutive nonlinear half-steps, imaginary
 // time renormalises the line after every step.
@@ -615,7 +642,10 @@ __global__ void __launch_bounds__(Tile<R, N, L, true>::NT) k_line1d(const Line1D
     extern __shared__ __align__(128) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
     double *red = reinterpret_cast<double *>(smraw + sizeof(C) * T::SMEM_POINTS);
-    U *tw = reinterpret_cast<U *>(smraw + sizeof(C) * T::SMEM_POINTS + sizeof(double) * T::NT);
+    // the reduction scratch is rounded up to 16 bytes so that the 16-byte
+    // twiddle entries after it stay aligned (tiles of one short line have an
+    // odd thread count)
+    U *tw = reinterpret_cast<U *>(smraw + sizeof(C) * T::SMEM_POINTS + line1d_red_bytes(T::NT));
     const int t = threadIdx.x, l = T::line_of(t), tl = T::tl_of(t);
     for (int i = t; i < N; i += T::NT) tw[i] = static_cast<const U *>(a.tw)[i];
     __syncthreads();
@@ -639,11 +669,15 @@ __global__ void __launch_bounds__(Tile<R, N, L, true>::NT) k_line1d(const Line1D
             const R gh = (R)(g * 0.5 * a.dt), gf = (R)(g * a.dt);
             const R invn = (R)(1.0 / N);
             // first nonlinear half-step
+            {
+                R th[E];
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                v[e] = cmadd1(v[e], phase_offset(gh * cabs2(v[e])));
-                if (vh) v[e] = uomul(v[e], vh[ib * N + tl + TPL * e]);
+                for (int e = 0; e < E; ++e) th[e] = gh * cabs2(v[e]);
+                apply_phase<C, R, E>(v, th);
             }
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (vh) v[e] = uomul(v[e], vh[ib * N + tl + TPL * e]);
 #pragma unroll 1
             for (int64_t st = 0; st < a.nsteps; ++st) {
                 T::template fft<-1>(v, sm, tl, l, tw);
@@ -653,11 +687,13 @@ __global__ void __launch_bounds__(Tile<R, N, L, true>::NT) k_line1d(const Line1D
                 const bool last = (st == a.nsteps - 1);
                 const R gc = last ? gh : gf;
                 const U *vt = last ? vh : vf;
+                R th[E];
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    v[e] = cmadd1(v[e], phase_offset(gc * cabs2(v[e])));
+                for (int e = 0; e < E; ++e) th[e] = gc * cabs2(v[e]);
+                apply_phase<C, R, E>(v, th);
+#pragma unroll
+                for (int e = 0; e < E; ++e)
                     if (vt) v[e] = uomul(v[e], vt[ib * N + tl + TPL * e]);
-                }
             }
         } else {
             const R *ki = static_cast<const R *>(a.kt);
@@ -752,12 +788,24 @@ static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st, const CUten
     return cudaGetLastError();
 }
 
-template <typename R, int N> static cudaError_t launch_line1d_t(const Line1DArgs &a, cudaStream_t st)
+static int sm_count()
 {
-    constexpr int L = pick_lines_1d<R, N>();
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!cached[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n > 0 ? n : 1;
+    }
+    return cached[dev];
+}
+
+template <typename R, int N, int L> static cudaError_t launch_line1d_l(const Line1DArgs &a, cudaStream_t st)
+{
     using T = Tile<R, N, L, true>;
     static LaunchCache lc;
-    const size_t smem = sizeof(typename T::C) * T::SMEM_POINTS + sizeof(double) * T::NT + sizeof(typename T::U) * N;
+    const size_t smem = sizeof(typename T::C) * T::SMEM_POINTS + line1d_red_bytes(T::NT) + sizeof(typename T::U) * N;
     int cap = 0;
     cudaError_t e = prepare(k_line1d<R, N, L>, lc, T::NT, smem, &cap);
     if (e != cudaSuccess) return e;
@@ -766,6 +814,18 @@ template <typename R, int N> static cudaError_t launch_line1d_t(const Line1DArgs
     const int grid = (int)(ntiles < cap ? ntiles : cap);
     k_line1d<R, N, L><<<grid, T::NT, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+// Fewer instances than SMs: one line per CTA, so that no warp spends the SM's
+// pipes on the empty lines of a part-filled tile (the per-line arithmetic is
+// the same either way).
+template <typename R, int N> static cudaError_t launch_line1d_t(const Line1DArgs &a, cudaStream_t st)
+{
+    constexpr int L = pick_lines_1d<R, N>();
+    if constexpr (L > 1) {
+        if (a.batch < sm_count()) return launch_line1d_l<R, N, 1>(a, st);
+    }
+    return launch_line1d_l<R, N, L>(a, st);
 }
 
 #define GPE_FOR_EACH_N(X) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
