@@ -283,10 +283,15 @@ template <typename R, int N, int L, bool ROWS> struct Tile {
 // distinct 128-byte bank rows when a point row (L points) is narrower than a
 // bank row.  The map is a bijection of [0, N): every flipped bit is flipped by
 // a higher bit, which it does not change.
-template <typename R, int N, int L, int LPT, bool SW = false> struct GTile {
+//
+// EPT points per thread (0: Radix<N>::E = 8): with 16, each pass runs two
+// butterflies per thread (more independent work per thread, half the threads
+// per line); the arithmetic of every butterfly is the same.
+template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struct GTile {
     using C = typename CT<R>::C;
     using U = typename UT<R>::U;
-    static constexpr int E = Radix<N>::E;
+    static constexpr int E = EPT ? EPT : Radix<N>::E;
+    static_assert(E >= Radix<N>::E && N % E == 0, "points per thread must cover the largest radix");
     static constexpr int TPL = N / E;
     static constexpr int NP = L / LPT;
     static constexpr int NT = NP * TPL;

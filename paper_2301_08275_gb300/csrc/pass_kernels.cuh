@@ -379,8 +379,19 @@ template <typename R> __host__ __device__ constexpr int lines_per_thread() { ret
 // shared by the thread's lines.  Tiles are software-pipelined: the points of
 // tile i+2 are copied into one of two shared buffers with cp.async while tile
 // i is transformed in the other.
+// points per thread: 16 for strided complex64 lines of at least 16 points (two
+// butterflies per thread and pass: the 512^3 y sweep 0.51 -> 0.45 ms, z 0.92 ->
+// 0.90 ms), else 8; rows keep 8 (16 measured slower there).  Every tile shape
+// of a pass kind uses the same count, so the per-line reductions add in the
+// same order whichever shape the tuner picks.
+template <typename R, int N, bool ROWS> __host__ __device__ constexpr int pass_points_per_thread()
+{
+    return (!ROWS && sizeof(R) == 4 && N >= 16) ? 16 : Radix<N>::E;
+}
+
 template <typename R, int N, bool ROWS, int VAR>
-using PassTile = GTile<R, N, pick_lines<R, N, ROWS, VAR>(), lines_per_thread<R>(), rows_split<R, N, ROWS, VAR>()>;
+using PassTile = GTile<R, N, pick_lines<R, N, ROWS, VAR>(), lines_per_thread<R>(), rows_split<R, N, ROWS, VAR>(),
+                       pass_points_per_thread<R, N, ROWS>()>;
 
 // dynamic shared memory of one CTA: two staging buffers, per-line reduction
 // scratch, twiddles, two mbarriers
