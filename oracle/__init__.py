@@ -85,6 +85,7 @@ def _load():
         lib.orc_spectrum_nshells.argtypes = [G]
         lib.orc_spectrum_nshells.restype = ctypes.c_long
         lib.orc_spectrum.argtypes = [cd, G, cd, cd, ctypes.c_long]
+        lib.orc_spectrum_qp_num.argtypes = [cd, G, cd, cd, ctypes.c_long]
         lib.orc_set_threads.argtypes = [ctypes.c_int]
         _lib = lib
         return lib
@@ -227,3 +228,13 @@ class Problem:
         _check(_load().orc_spectrum(_ptr(x), ctypes.byref(self._g), _ptr(ei), _ptr(ec), ns),
                "spectrum")
         return ei, ec
+
+    def spectrum_qp_num(self, psi):
+        """Returns (E_qp[nshells], N[nshells]): quantum-pressure and particle-number spectra."""
+        x = _as_c128(psi, self.N)
+        ns = self.nshells()
+        eq = np.zeros(ns)
+        nn = np.zeros(ns)
+        _check(_load().orc_spectrum_qp_num(_ptr(x), ctypes.byref(self._g), _ptr(eq), _ptr(nn), ns),
+               "spectrum_qp_num")
+        return eq, nn

@@ -532,6 +532,64 @@ int orc_spectrum(const cplx *psi, const orc_grid *G, double *e_inc, double *e_co
     return 0;
 }
 
+/* Quantum-pressure and particle-number spectra (the decomposition of the
+ * kinetic energy in the feature list, item 3, completed by its third part):
+ *   w_a = Re(conj(psi) d_a psi)/|psi| = d_a |psi| (0 where |psi|^2 < 1e-30),
+ *   E_qp(n) = 1/2 sum_{shell n} sum_a |FFT(w_a)|^2 dV/N;
+ *   N(n) = sum_{shell n} |psi_hat|^2 dV/N   (sum over shells = norm).
+ * d_a psi as in orc_spectrum.  e_qp / n_num may be NULL. */
+int orc_spectrum_qp_num(const cplx *psi, const orc_grid *G, double *e_qp, double *n_num, long nshells)
+{
+    int e = check_grid(G);
+    if (e) return e;
+    long need = orc_spectrum_nshells(G);
+    if (nshells < need) return -1;
+    long N = total_points(G);
+    int d = G->ndim;
+    double dv = cell_volume(G);
+    cplx *ph = (cplx *)malloc(sizeof(cplx) * (size_t)N);
+    cplx *wh = (cplx *)malloc(sizeof(cplx) * (size_t)N);
+    if (!ph || !wh) return -4;
+    memcpy(ph, psi, sizeof(cplx) * (size_t)N);
+    orc_fft(ph, d, G->n, -1);
+    if (e_qp) memset(e_qp, 0, sizeof(double) * (size_t)nshells);
+    if (n_num) memset(n_num, 0, sizeof(double) * (size_t)nshells);
+    if (n_num) {
+        for (long i = 0; i < N; i++) {
+            long j[3];
+            unflatten(G, i, j);
+            n_num[shell_of(G, j)] += (creal(ph[i]) * creal(ph[i]) + cimag(ph[i]) * cimag(ph[i])) * dv / (double)N;
+        }
+    }
+    if (e_qp) {
+        for (int a = 0; a < d; a++) {
+            for (long i = 0; i < N; i++) {
+                long j[3];
+                unflatten(G, i, j);
+                double k = (2 * j[a] == G->n[a]) ? 0.0 : wavenumber(G, a, j[a]);
+                wh[i] = I * k * ph[i];
+            }
+            orc_fft(wh, d, G->n, +1);
+            for (long i = 0; i < N; i++) {
+                cplx dpsi = wh[i] / (double)N;
+                double rho = creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);
+                double w = 0.0;
+                if (rho >= 1e-30) w = creal(conj(psi[i]) * dpsi) / sqrt(rho);
+                wh[i] = w;
+            }
+            orc_fft(wh, d, G->n, -1);
+            for (long i = 0; i < N; i++) {
+                long j[3];
+                unflatten(G, i, j);
+                e_qp[shell_of(G, j)] += 0.5 * (creal(wh[i]) * creal(wh[i]) + cimag(wh[i]) * cimag(wh[i])) * dv / (double)N;
+            }
+        }
+    }
+    free(wh);
+    free(ph);
+    return 0;
+}
+
 /* thread control for the timed CPU baseline */
 int orc_set_threads(int nt)
 {

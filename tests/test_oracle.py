@@ -372,3 +372,58 @@ def test_sampled_potential_follows_the_grid_points(orc):
     e = orc.Problem(**dict(sp.kwargs(), gamma=(0.0, 0.0, 0.0)), V=lat).norm_energy(psi0)
     dv = np.prod([sp.length[i] / sp.n[i] for i in range(3)])
     assert abs(e[2] - np.sum(lat * np.abs(psi0) ** 2) * dv) < 1e-12 * abs(e[2])
+
+
+# ------------------------------------------------ quantum-pressure / number spectra
+def _band_limited(sp, seed, kmax_frac=0.25):
+    """Smooth complex field whose Fourier modes all lie below kmax_frac * n/2 on
+    every axis, with |psi| bounded away from 0 (no Nyquist content, no zeros)."""
+    rng = np.random.default_rng(seed)
+    ph = np.zeros(sp.shape, complex)
+    sl = tuple(slice(0, max(1, int(kmax_frac * n / 2))) for n in reversed(sp.n))
+    ph[sl] = rng.normal(size=ph[sl].shape) + 1j * rng.normal(size=ph[sl].shape)
+    f = np.fft.ifftn(ph)
+    f = f / np.max(np.abs(f))
+    return 2.0 + f + 0.3j * np.conj(f) * f
+
+
+@pytest.mark.parametrize("sp", [
+    gi.Spec(n=(32, 16), lo=(0, 0), length=(8.0, 4.0), g=1.0, gamma=(0.0, 0.0)),
+    gi.Spec(n=(16, 8, 32), lo=(0, 0, 0), length=(4.0, 2.0, 8.0), g=1.0, gamma=(0.0, 0.0, 0.0)),
+])
+def test_spectra_add_up_to_the_kinetic_energy_and_the_norm(orc, sp):
+    """|grad psi|^2 = |grad |psi||^2 + |psi|^2 |grad theta|^2 point by point, so the
+    incompressible, compressible and quantum-pressure spectra sum to E_kin (for a
+    field without Nyquist content); the particle-number spectrum sums to the norm."""
+    P = orc.Problem(**sp.kwargs())
+    psi = _band_limited(sp, seed=7)
+    ei, ec = P.spectrum(psi)
+    eq, nn = P.spectrum_qp_num(psi)
+    e = P.norm_energy(psi)
+    assert abs(ei.sum() + ec.sum() + eq.sum() - e[1]) < 1e-11 * e[1]
+    assert abs(nn.sum() - e[0]) < 1e-12 * e[0]
+
+
+def test_real_positive_field_is_all_quantum_pressure(orc):
+    sp = gi.Spec(n=(32, 32), lo=(-4, -4), length=(8.0, 8.0), g=1.0, gamma=(0.0, 0.0))
+    psi = np.abs(_band_limited(sp, seed=3)).astype(complex)
+    psi = np.real(np.fft.ifftn(np.where(np.abs(np.fft.fftfreq(32))[None, :] < 0.2, 1, 0)
+                               * np.where(np.abs(np.fft.fftfreq(32))[:, None] < 0.2, 1, 0)
+                               * np.fft.fftn(psi))).astype(complex) + 0.5
+    P = orc.Problem(**sp.kwargs())
+    ei, ec = P.spectrum(psi)
+    eq, nn = P.spectrum_qp_num(psi)
+    e = P.norm_energy(psi)
+    assert ei.sum() < 1e-25 and ec.sum() < 1e-25
+    assert abs(eq.sum() - e[1]) < 1e-11 * e[1]
+
+
+def test_uniform_density_plane_wave_has_no_quantum_pressure(orc):
+    sp = gi.Spec(n=(32, 16), lo=(0, 0), length=(2 * math.pi * 2, 2 * math.pi), g=1.0, gamma=(0.0, 0.0))
+    psi = gi.plane_wave(sp, (3, -2), 0.8)
+    P = orc.Problem(**sp.kwargs())
+    eq, nn = P.spectrum_qp_num(psi)
+    assert eq.sum() < 1e-25
+    # all particles sit in the plane wave's shell: n = round(|m| dk_ratio) for m = (3, -2)
+    k = math.sqrt(3 ** 2 + (2 * 2) ** 2)          # mode numbers in units of 2 pi / max L
+    assert abs(nn[int(round(k))] - P.norm_energy(psi)[0]) < 1e-12 * nn.sum()
