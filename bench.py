@@ -667,13 +667,107 @@ def run_trap(args):
     return 0
 
 
+def run_table1(args):
+    """The paper's Table 1, 2D block, as a served batch: the seven ground states
+    (g from -2.5 to 627) by imaginary time through the request server at once,
+    complex128, 128^2 on [-10, 10)^2, dt = 1e-3, |dE| < 1e-12 checked every 50
+    steps.  value = wall time to the last ground state; r_rms and mu are
+    compared with the printed values."""
+    import torch
+    import paper_2301_08275_gb300 as gpe
+    gpe.build()
+    torch.cuda.set_device(0)
+    rows = json.load(open(os.path.join(ROOT, "tests", "golden", "table1_2d.json")))["rows"]
+    specs = [gi.Spec(n=(128, 128), lo=(-10.0, -10.0), length=(20.0, 20.0), g=float(r[0]), dt=1e-3,
+                     gamma=(1.0, 1.0)) for r in rows]
+    psi0 = [gi.harmonic_gaussian(sp) for sp in specs]
+    srv = gpe.gpe_server_create(4 << 30, max_active=8, chunk_steps=500)
+    t0 = time.perf_counter()
+    tickets = [gpe.gpe_serve_submit(srv, gpe.make_desc(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma,
+                                                       prec=gpe.GPE_C128)[0], ps, imag=True, nsteps=60000,
+                                    etol=1e-12, check_every=50) for sp, ps in zip(specs, psi0)]
+    outs, res = [], []
+    for sp, t in zip(specs, tickets):
+        o = np.empty(sp.shape, np.complex128)
+        res.append(gpe.gpe_serve_poll(srv, t, timeout_ms=-1, psi_out=o))
+        outs.append(o)
+    wall = time.perf_counter() - t0
+    gpe.gpe_server_destroy(srv)
+    table, worst = [], 0.0
+    for (g_, r_ref, mu_ref), sp, o, r in zip(rows, specs, outs, res):
+        p = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma, prec=gpe.GPE_C128)
+        x = torch.from_numpy(o).cuda()
+        rr = float(p.rms_size(x)[0][3])
+        mu = float(p.norm_energy(x)[0][5])
+        p.close()
+        dev = max(abs(rr - r_ref) / r_ref, abs(mu - mu_ref) / mu_ref)
+        worst = max(worst, dev)
+        table.append({"g": g_, "steps": int(r.steps_done), "r_rms": rr, "r_rms_paper": r_ref, "mu": mu,
+                      "mu_paper": mu_ref, "rel_dev": dev})
+    steps = sum(t["steps"] for t in table)
+    line = {"metric": "Table 1 (2D) ground states served together: wall time", "value": wall, "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "f64",
+            "updates_per_s": 128 * 128 * steps / wall, "max_rel_dev_from_paper": worst, "rows": table,
+            "config": {"workload": "paper Table 1 2D block: 7 imaginary-time ground states, 128^2 on [-10,10)^2, "
+                                   "dt=1e-3, |dE|<1e-12 every 50 steps, complex128, request server"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_bao(args):
+    """The paper's dynamics validation: 3D anisotropic Gaussian (gamma_y = 2,
+    gamma_z = 4, eps1 = 0.25), V = (x^2 + 4 y^2 + 16 z^2)/2, g = 0.1, 128^3,
+    complex64, dt = 1e-3; `--steps` real-time steps with the rms sizes read
+    every 100 steps.  value = grid-point updates/s including the reads; the
+    sizes are reported beside the g = 0 closed form."""
+    import math
+    import torch
+    import paper_2301_08275_gb300 as gpe
+    gpe.build()
+    torch.cuda.set_device(0)
+    eps = 0.25
+    sp = gi.Spec(n=(128, 128, 128), lo=(-8.0, -6.0, -4.5), length=(16.0, 12.0, 9.0), g=0.1, dt=1e-3,
+                 gamma=(1.0, 2.0, 4.0))
+    stream = torch.cuda.Stream()
+    p = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma, prec=gpe.GPE_C64, stream=stream)
+    psi = torch.from_numpy(gi.bao_gaussian(sp).astype(np.complex64)).cuda()
+    torch.cuda.synchronize()
+    tiles = p.autotune(psi, reps=3)
+    w = psi.clone()
+    p.step_real(w, max(3, args.warmup))
+    del w
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    series = []
+    e0.record(stream)
+    for s0 in range(0, args.steps, 100):
+        k = min(100, args.steps - s0)
+        p.step_real(psi, k)
+        r = p.rms_size(psi)[0]
+        t = (s0 + k) * sp.dt
+        ex = [math.sqrt(eps / (2 * ga) * math.cos(ga * t) ** 2 + 1 / (2 * ga * eps) * math.sin(ga * t) ** 2)
+              for ga in (1.0, 2.0, 4.0)]
+        series.append({"t": round(t, 6), "sigma": [float(v) for v in r[:3]], "sigma_g0_closed_form": ex})
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    line = {"metric": "TSSP grid-point updates/s (dynamics validation run)", "value": sp.N * args.steps / (ms / 1e3),
+            "unit": "grid-point updates/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+            "ms_per_step": ms / args.steps, "data": "synthetic", "dtype": "f32", "tiles": tiles,
+            "config": {"workload": "paper dynamics validation: 3D anisotropic Gaussian, gamma=(1,2,4), eps1=0.25, "
+                                   "g=0.1, 128^3 on [-8,8)x[-6,6)x[-4.5,4.5), dt=1e-3, complex64, rms every 100 steps"},
+            "sigma_series": series}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tg512", choices=sorted(WORKLOADS) + ["batched", "serving", "trap256"])
+    ap.add_argument("--workload", default="tg512", choices=sorted(WORKLOADS) + ["batched", "serving", "trap256", "table1", "bao128"])
     ap.add_argument("--imag-max", type=int, default=20000, help="trap256: imaginary-time step limit")
     ap.add_argument("--instances", type=int, default=512, help="batched: number of instances")
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
@@ -692,6 +786,10 @@ def main():
         return run_serving(args)
     if args.workload == "trap256":
         return run_trap(args)
+    if args.workload == "table1":
+        return run_table1(args)
+    if args.workload == "bao128":
+        return run_bao(args)
     wl = dict(WORKLOADS[args.workload])
     if args.grid:
         sp = wl["spec"]

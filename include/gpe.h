@@ -126,11 +126,19 @@ gpe_status gpe_rms_size(gpe_plan *plan, const void *psi_dev, double *out_host);
  * |psi|^2 < 1e-30); u_hat = FFT u split into u_c = k(k.u_hat)/|k|^2 and
  * u_i = u_hat - u_c; E(n) = 1/2 sum over shell n of |u|^2 dV/N with
  * n = round(|k| / dk), dk = 2 pi / max_a len_a.
- * kinds: GPE_SPEC_INC | GPE_SPEC_COMP.  out_host receives, for each requested
- * kind in that order, nshells doubles per instance ([kind][b][shell]).
+ * The kinetic energy splits further into a quantum-pressure part:
+ * GPE_SPEC_QP bins 1/2 sum_a |FFT w_a|^2 dV/N with w_a = Re(conj(psi) d_a psi)/|psi|
+ * = d_a |psi|, so that INC + COMP + QP summed over shells is E_kin for fields
+ * without Nyquist content; GPE_SPEC_NUM bins the particle number
+ * |psi_hat|^2 dV/N (its sum is the norm).
+ * kinds: any non-empty combination of GPE_SPEC_INC, GPE_SPEC_COMP,
+ * GPE_SPEC_QP, GPE_SPEC_NUM.  out_host receives, for each requested kind in
+ * that order, nshells doubles per instance ([kind][b][shell]).
  * nshells must be >= gpe_spectrum_nshells(plan). */
 #define GPE_SPEC_INC 1u
 #define GPE_SPEC_COMP 2u
+#define GPE_SPEC_QP 4u
+#define GPE_SPEC_NUM 8u
 int64_t gpe_spectrum_nshells(const gpe_plan *plan);
 gpe_status gpe_spectrum(gpe_plan *plan, const void *psi_dev, unsigned kinds, double *out_host,
                         int64_t nshells);

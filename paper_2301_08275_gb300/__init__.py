@@ -22,7 +22,7 @@ _lock = threading.Lock()
 _lib = None
 
 GPE_C64, GPE_C128 = 0, 1
-GPE_SPEC_INC, GPE_SPEC_COMP = 1, 2
+GPE_SPEC_INC, GPE_SPEC_COMP, GPE_SPEC_QP, GPE_SPEC_NUM = 1, 2, 4, 8
 STATUS = {0: "GPE_OK", 1: "GPE_EINVAL", 2: "GPE_EUNSUPPORTED", 3: "GPE_ENOMEM", 4: "GPE_ECUDA",
           5: "GPE_ENUMERIC", 6: "GPE_ETIMEOUT", 7: "GPE_EBUSY", 8: "GPE_ENOTREADY"}
 
@@ -194,7 +194,7 @@ def gpe_spectrum_nshells(plan):
 
 def gpe_spectrum(plan, psi_ptr, kinds, batch):
     ns = gpe_spectrum_nshells(plan)
-    nk = bin(int(kinds) & 3).count("1")
+    nk = bin(int(kinds) & 15).count("1")
     out = np.zeros(nk * batch * ns)
     _check(lib().gpe_spectrum(plan, ctypes.c_void_p(psi_ptr), int(kinds), _dptr(out), ns))
     return out.reshape(nk, batch, ns)

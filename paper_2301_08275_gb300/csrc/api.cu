@@ -1153,8 +1153,10 @@ extern "C" gpe_status gpe_spectrum(gpe_plan *p, const void *psi, unsigned kinds,
 {
     GPE_TRY(check_psi(p, psi));
     if (!out) return fail(GPE_EINVAL, "NULL output");
-    if (!(kinds & (GPE_SPEC_INC | GPE_SPEC_COMP)) || (kinds & ~(GPE_SPEC_INC | GPE_SPEC_COMP)))
-        return fail(GPE_EINVAL, "kinds must be a non-empty combination of GPE_SPEC_INC and GPE_SPEC_COMP");
+    const unsigned all = GPE_SPEC_INC | GPE_SPEC_COMP | GPE_SPEC_QP | GPE_SPEC_NUM;
+    if (!(kinds & all) || (kinds & ~all))
+        return fail(GPE_EINVAL, "kinds must be a non-empty combination of GPE_SPEC_INC, GPE_SPEC_COMP, "
+                                "GPE_SPEC_QP and GPE_SPEC_NUM");
     const int64_t ns = nshells_of(p);
     if (nshells < ns) return fail(GPE_EINVAL, "nshells smaller than gpe_spectrum_nshells()");
     if (ns > 6144) return fail(GPE_EUNSUPPORTED, "too many spectral shells");
@@ -1182,34 +1184,62 @@ extern "C" gpe_status gpe_spectrum(gpe_plan *p, const void *psi, unsigned kinds,
         p->nshells = ns;
         p->hist_blocks = nb;
     }
+    // output slot of each kind: requested kinds in bit order
+    double *slot[4] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<double> tmp(2 * ns);
-    const int nk = ((kinds & GPE_SPEC_INC) ? 1 : 0) + ((kinds & GPE_SPEC_COMP) ? 1 : 0);
-    for (int64_t b = 0; b < p->batch; ++b) {
-        const char *pb = (const char *)psi + (size_t)b * field;
-        GPE_TRY(fft_nd(p, pb, p->work[0], -1));
-        for (int a = 0; a < p->ndim; ++a) {
-            cudaError_t e = launch_deriv(sa, p->work[0], p->work[1 + a], a, p->st);
-            if (e != cudaSuccess) return fail(GPE_ECUDA, cudaGetErrorString(e));
-            GPE_TRY(fft_nd(p, p->work[1 + a], p->work[1 + a], +1));
-            e = launch_velocity(sa, pb, p->work[1 + a], p->st);
-            if (e != cudaSuccess) return fail(GPE_ECUDA, cudaGetErrorString(e));
-            GPE_TRY(fft_nd(p, p->work[1 + a], p->work[1 + a], -1));
-        }
-        void *uh[3] = {p->work[1], p->ndim > 1 ? p->work[2] : nullptr, p->ndim > 2 ? p->work[3] : nullptr};
-        cudaError_t e = launch_bin(sa, uh, ns, p->hist, nb, p->st);
+    // bin the given fields and write shells (scaled) into o0 / o1 (either may be NULL)
+    auto bin_out = [&](void *const *uh, int split, int ncomp, double scale, double *o0, double *o1) -> gpe_status {
+        SpecArgs sb = sa;
+        sb.split = split;
+        sb.ncomp = ncomp;
+        cudaError_t e = launch_bin(sb, uh, ns, p->hist, nb, p->st);
         if (e == cudaSuccess)
             e = launch_hist_reduce(p->hist, nb, ns, p->dv / (double)p->N, p->spec_out, p->spec_out + ns, p->st);
         if (e != cudaSuccess) return fail(GPE_ECUDA, cudaGetErrorString(e));
         GPE_CUDA(cudaMemcpyAsync(tmp.data(), p->spec_out, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost, p->st));
         GPE_CUDA(cudaStreamSynchronize(p->st));
-        int kslot = 0;
-        for (int kind = 0; kind < 2; ++kind) {
-            if (!(kinds & (kind == 0 ? GPE_SPEC_INC : GPE_SPEC_COMP))) continue;
-            double *dst = out + ((size_t)kslot * p->batch + b) * nshells;
-            for (int64_t s = 0; s < nshells; ++s) dst[s] = s < ns ? tmp[kind * ns + s] : 0.0;
-            ++kslot;
+        double *o[2] = {o0, o1};
+        for (int k = 0; k < 2; ++k)
+            if (o[k])
+                for (int64_t s2 = 0; s2 < nshells; ++s2) o[k][s2] = s2 < ns ? scale * tmp[k * ns + s2] : 0.0;
+        return GPE_OK;
+    };
+    // derivative fields -> u (part 0) or w (part 1) -> their transforms, in work[1..ndim]
+    auto gradient_parts = [&](const void *pb, int part) -> gpe_status {
+        SpecArgs sv = sa;
+        sv.part = part;
+        for (int a = 0; a < p->ndim; ++a) {
+            cudaError_t e = launch_deriv(sa, p->work[0], p->work[1 + a], a, p->st);
+            if (e != cudaSuccess) return fail(GPE_ECUDA, cudaGetErrorString(e));
+            GPE_TRY(fft_nd(p, p->work[1 + a], p->work[1 + a], +1));
+            e = launch_velocity(sv, pb, p->work[1 + a], p->st);
+            if (e != cudaSuccess) return fail(GPE_ECUDA, cudaGetErrorString(e));
+            GPE_TRY(fft_nd(p, p->work[1 + a], p->work[1 + a], -1));
         }
-        (void)nk;
+        return GPE_OK;
+    };
+    void *uh[3] = {p->work[1], p->ndim > 1 ? p->work[2] : nullptr, p->ndim > 2 ? p->work[3] : nullptr};
+    for (int64_t b = 0; b < p->batch; ++b) {
+        int kslot = 0;
+        for (int k = 0; k < 4; ++k) {
+            slot[k] = nullptr;
+            if (kinds & (1u << k)) slot[k] = out + ((size_t)kslot++ * p->batch + b) * nshells;
+        }
+        const char *pb = (const char *)psi + (size_t)b * field;
+        GPE_TRY(fft_nd(p, pb, p->work[0], -1));
+        if (slot[3]) {
+            // the bins carry 1/2 dV/N; the number spectrum has no 1/2
+            void *ph[3] = {p->work[0], nullptr, nullptr};
+            GPE_TRY(bin_out(ph, 0, 1, 2.0, slot[3], nullptr));
+        }
+        if (slot[0] || slot[1]) {
+            GPE_TRY(gradient_parts(pb, 0));
+            GPE_TRY(bin_out(uh, 1, p->ndim, 1.0, slot[0], slot[1]));
+        }
+        if (slot[2]) {
+            GPE_TRY(gradient_parts(pb, 1));
+            GPE_TRY(bin_out(uh, 0, p->ndim, 1.0, slot[2], nullptr));
+        }
     }
     return GPE_OK;
 }

@@ -120,7 +120,8 @@ __global__ void k_deriv(const SpecArgs s, const typename CT<R>::C *__restrict__ 
     }
 }
 
-// w <- u = Im(conj(psi) * w / N) / |psi|  (0 where |psi|^2 < 1e-30), stored as (u, 0).
+// w <- u = Im(conj(psi) * w / N) / |psi| (part 0) or Re(...) / |psi| (part 1: the
+// gradient of |psi|), 0 where |psi|^2 < 1e-30, stored as (u, 0).
 template <typename R>
 __global__ void k_velocity(const SpecArgs s, const typename CT<R>::C *__restrict__ psi, typename CT<R>::C *__restrict__ w)
 {
@@ -131,13 +132,13 @@ __global__ void k_velocity(const SpecArgs s, const typename CT<R>::C *__restrict
         const C d = w[i];
         const R rho = p.x * p.x + p.y * p.y;
         R u = (R)0;
-        if (rho >= (R)1e-30) u = (p.x * d.y - p.y * d.x) * invn / sqrt(rho);
+        if (rho >= (R)1e-30) u = (s.part ? (p.x * d.x + p.y * d.y) : (p.x * d.y - p.y * d.x)) * invn / sqrt(rho);
         w[i] = mk(u, (R)0);
     }
 }
 
-// Shell histogram of |u_i|^2 and |u_c|^2 over the k grid, one partial
-// histogram per block (hist[block][2][nshells]).
+// Shell histogram of |u_i|^2 and |u_c|^2 (split) or of sum_a |u_a|^2 (slot 0)
+// over the k grid, one partial histogram per block (hist[block][2][nshells]).
 template <typename R>
 __global__ void k_bin(const SpecArgs s, const typename CT<R>::C *__restrict__ u0, const typename CT<R>::C *__restrict__ u1,
                       const typename CT<R>::C *__restrict__ u2, int64_t nshells, double *__restrict__ hist)
@@ -159,6 +160,16 @@ __global__ void k_bin(const SpecArgs s, const typename CT<R>::C *__restrict__ u0
             const double qa = (double)m * s.lratio[a];
             q2 += qa * qa;
         }
+        const int64_t sh_i = (int64_t)floor(sqrt(q2) + 0.5);
+        if (!s.split) {
+            double et = 0.0;
+            for (int a = 0; a < s.ncomp; ++a) {
+                const C v = u[a][i];
+                et += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+            }
+            atomicAdd(&sh[sh_i], et);
+            continue;
+        }
         double ur[3] = {0, 0, 0}, ui[3] = {0, 0, 0}, kdr = 0.0, kdi = 0.0;
         for (int a = 0; a < s.ndim; ++a) {
             const C v = u[a][i];
@@ -174,7 +185,6 @@ __global__ void k_bin(const SpecArgs s, const typename CT<R>::C *__restrict__ u0
             ec += cr * cr + ci * ci;
             ei += (ur[a] - cr) * (ur[a] - cr) + (ui[a] - ci) * (ui[a] - ci);
         }
-        const int64_t sh_i = (int64_t)floor(sqrt(q2) + 0.5);
         atomicAdd(&sh[sh_i], ei);
         atomicAdd(&sh[nshells + sh_i], ec);
     }

@@ -129,6 +129,9 @@ struct SpecArgs {
     double kf[3];       // 2 pi / len
     double lratio[3];   // max_len / len
     int64_t N;
+    int part;           // k_velocity: 0 u = Im(conj(psi) d psi)/|psi|, 1 w = Re(...)/|psi| = d|psi|
+    int split;          // k_bin: 1 incompressible / compressible parts, 0 total of the components
+    int ncomp;          // k_bin: field components summed (ndim, or 1 for psi_hat itself)
 };
 cudaError_t launch_deriv(const SpecArgs &s, const void *src, void *dst, int axis, cudaStream_t st);
 cudaError_t launch_velocity(const SpecArgs &s, const void *psi, void *w, cudaStream_t st);

@@ -429,3 +429,45 @@ def test_1d_small_and_full_tiles_give_the_same_bits(gpe, prec):
             torch.cuda.synchronize()
             assert np.array_equal(y.cpu().numpy(), allb[b]), (imag, b)
         p1.close()
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_quantum_pressure_and_number_spectra_match_oracle(gpe, orc, prec):
+    """All four spectra in one call, in kind order, against the oracle (2D
+    vortex field), and INC + COMP + QP summed against E_kin of the same state."""
+    pv = gpe.GPE_C128 if prec == "c128" else gpe.GPE_C64
+    sp = gi.Spec(n=(128, 128), lo=(0, 0), length=(2 * math.pi * 8,) * 2, g=1.0)
+    psi, _, _ = gi.vortex_field_2d(sp, nv=16, seed=4)
+    if prec == "c64":
+        psi = psi.astype(np.complex64).astype(np.complex128)
+    pr = P(orc, sp)
+    ei, ec = pr.spectrum(psi)
+    eq, nn = pr.spectrum_qp_num(psi)
+    p = plan_for(gpe, sp, pv)
+    x = to_dev(psi, pv, gpe)
+    k = gpe.GPE_SPEC_INC | gpe.GPE_SPEC_COMP | gpe.GPE_SPEC_QP | gpe.GPE_SPEC_NUM
+    out = p.spectrum(x, kinds=k)
+    assert out.shape == (4, 1, len(ei))
+    tol = 1e-10 if prec == "c128" else 1e-4
+    for got, ref in zip(out[:, 0], (ei, ec, eq, nn)):
+        assert np.max(np.abs(got - ref)) < tol * ref.max()
+    e = p.norm_energy(x)[0]
+    assert abs(out[3, 0].sum() - e[0]) < (1e-12 if prec == "c128" else 1e-6) * e[0]
+    # |grad psi|^2 = |grad|psi||^2 + |psi|^2 |grad theta|^2: the three parts sum to E_kin
+    # (to 7e-11 in the oracle for this field: its Nyquist content is that small)
+    assert abs(out[0, 0].sum() + out[1, 0].sum() + out[2, 0].sum() - e[1]) < (1e-9 if prec == "c128" else 1e-5) * e[1]
+    only = p.spectrum(x, kinds=gpe.GPE_SPEC_QP)
+    # shells are accumulated with atomic adds, so repeated calls agree to rounding
+    assert only.shape == (1, 1, len(eq)) and np.allclose(only[0, 0], out[2, 0], rtol=1e-12, atol=0)
+    p.close()
+
+
+def test_quantum_pressure_spectrum_3d_matches_oracle(gpe, orc):
+    sp = gi.Spec(n=(16, 32, 8), lo=(0, 0, 0), length=(2 * math.pi, 4 * math.pi, 2 * math.pi), g=1.0)
+    psi = gi.random_field(sp, seed=8, smooth=0.02) + 2.0
+    eq, nn = P(orc, sp).spectrum_qp_num(psi)
+    p = plan_for(gpe, sp, gpe.GPE_C128)
+    out = p.spectrum(to_dev(psi, gpe.GPE_C128, gpe), kinds=gpe.GPE_SPEC_QP | gpe.GPE_SPEC_NUM)
+    assert np.max(np.abs(out[0, 0] - eq)) < 1e-10 * eq.max()
+    assert np.max(np.abs(out[1, 0] - nn)) < 1e-10 * nn.max()
+    p.close()
