@@ -100,16 +100,19 @@ __device__ __forceinline__ void apply_phase(C (&v)[E], const R (&th)[E])
 // copy bandwidth.  VAR 1: 4096 points / 8 lines, two CTAs per SM.
 // complex128 VAR 0: 2048 points / 4 lines (64-byte pieces), two CTAs per SM;
 // VAR 1: 4096 points / 8 lines.
-// Contiguous rows (x).  A split tile holds half the points and lines (4 rows
-// of complex64 at four CTAs per SM) with the swizzled shared layout: each
-// lane's points lie in its own row, and fewer rows per warp request with
-// longer pieces of each (4 rows x 64 bytes rather than 8 x 32) measured faster
-// for complex64 rows of up to 512 points.  VAR 0 splits exactly those; VAR 1
-// takes the other choice for every row length of at least 8.
+// Contiguous rows (x).  A split tile holds a fraction of the points and lines
+// with the swizzled shared layout and several CTAs per SM: each lane's points
+// lie in its own row, and fewer rows per warp request with longer pieces of
+// each measured faster for complex64 rows of up to 512 points.  Rows of 256
+// or 512 points: 2 rows (shape 0; 16 points = 128 bytes of each row per warp
+// request) or 4 (shape 1) - 512^3 x pass 0.945 -> 0.895 ms; 4 beat 8 (1.27 ->
+// 1.07 ms).  Shorter complex64 rows (tiny CTAs otherwise): 4 rows (shape 0)
+// or the unsplit tile (shape 1).  Longer or complex128 rows: shape 0 is the
+// unsplit tile, shape 1 the half tile.
 template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr bool rows_split()
 {
-    constexpr bool dflt = sizeof(R) == 4 && N <= 512;
-    return ROWS && N >= 8 && (VAR == 0 ? dflt : !dflt);
+    constexpr bool short_c64 = sizeof(R) == 4 && N <= 512;
+    return ROWS && N >= 8 && (short_c64 ? (N >= 256 || VAR == 0) : VAR == 1);
 }
 template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr int pick_lines()
 {
@@ -117,8 +120,10 @@ template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr i
     int maxpts = c64 ? 4096 : 2048, lmax = c64 ? 8 : 4;
     if (ROWS) {
         if (rows_split<R, N, ROWS, VAR>()) {
-            maxpts /= 2;
-            lmax /= 2;
+            // complex64 rows of 256 or 512 points: 2 rows per tile (shape 0) or 4 (shape 1)
+            const bool quarter = c64 && N >= 256 && N <= 512 && VAR == 0;
+            maxpts /= quarter ? 4 : 2;
+            lmax /= quarter ? 4 : 2;
         }
     } else if (c64 ? VAR == 0 : VAR == 1) {
         maxpts *= 2;
