@@ -177,13 +177,14 @@ gpe_status gpe_plan_get_option(const gpe_plan *plan, int option, int64_t *value)
 
 /* Autotuner (no counterpart in the paper): for every axis the plan sweeps,
  * times each tile shape (and, on y/z, each staging mode unless
- * GPE_TUNE_NO_TMA) on a scratch copy of psi_dev (the caller's array is only
- * read), `reps` launches per candidate of the pass that the steady real-time
- * step makes along that axis, and sets the options of the fastest.  Choices
- * are remembered per grid, precision and instance count for the life of the
- * process, so later plans of the same shape tune without timing.  Needs one
- * state-sized device scratch array for the duration of the call; synchronises
- * the plan stream.  1D plans have nothing to tune (GPE_OK). */
+ * GPE_TUNE_NO_TMA) on the state that axis's pass meets inside a real-time
+ * step (psi_dev, or zeros when psi_dev is NULL, advanced through the step's
+ * earlier passes; the caller's array is only read), `reps` launches per
+ * candidate, and sets the options of the fastest.  Choices are remembered per
+ * grid, precision and instance count for the life of the process, so later
+ * plans of the same shape tune without timing.  Needs two state-sized device
+ * scratch arrays for the duration of the call; synchronises the plan stream.
+ * 1D plans have nothing to tune (GPE_OK). */
 #define GPE_TUNE_NO_TMA 1
 gpe_status gpe_plan_autotune(gpe_plan *plan, const void *psi_dev, int reps, int flags);
 

@@ -908,9 +908,18 @@ extern "C" gpe_status gpe_plan_autotune(gpe_plan *p, const void *psi, int reps, 
             return GPE_OK;
         }
     }
+    // Each candidate is timed on the state its pass meets inside a step: prep
+    // holds psi advanced through the step's earlier passes (prologue, then the
+    // pivot pass, then the y inverse pass in 3D), and buf gets a fresh copy of
+    // prep before every timed launch.  (The x pass in particular must see
+    // physical |psi|: its nonlinear phase takes a cheaper path for small angles.)
     const size_t bytes = (size_t)B * (size_t)p->N * p->csize;
-    void *buf = nullptr;
+    void *buf = nullptr, *prep = nullptr;
     GPE_CUDA(cudaMalloc(&buf, bytes));
+    if (cudaMalloc(&prep, bytes) != cudaSuccess) {
+        cudaFree(buf);
+        return fail(GPE_ENOMEM, "autotune scratch");
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     gpe_status st = GPE_OK;
     TuneVal best;
@@ -920,9 +929,29 @@ extern "C" gpe_status gpe_plan_autotune(gpe_plan *p, const void *psi, int reps, 
     }
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         st = fail(GPE_ECUDA, "cudaEventCreate failed");
-    if (st == GPE_OK && !psi && cudaMemsetAsync(buf, 0, bytes, p->st) != cudaSuccess)
-        st = fail(GPE_ECUDA, "cudaMemsetAsync failed");
-    for (int a = 0; a < p->ndim && st == GPE_OK; ++a) {
+    if (st == GPE_OK) {
+        cudaError_t e = psi ? cudaMemcpyAsync(prep, psi, bytes, cudaMemcpyDeviceToDevice, p->st)
+                            : cudaMemsetAsync(prep, 0, bytes, p->st);
+        if (e != cudaSuccess) st = fail(GPE_ECUDA, "scratch set-up failed");
+    }
+    // prologue of a real-time step: first nonlinear half-step with FFT_x, then FFT_y (3D)
+    if (st == GPE_OK) {
+        PassArgs x0 = make_pass(p, 0, prep, prep, B);
+        x0.op_pre = OP_NREAL;
+        set_nreal(p, x0, false);
+        x0.fft1 = -1;
+        st = run(p, x0);
+    }
+    if (st == GPE_OK && p->ndim == 3) {
+        PassArgs y = make_pass(p, 1, prep, prep, B);
+        y.fft1 = -1;
+        st = run(p, y);
+    }
+    const int piv = p->ndim - 1;
+    const int order[3] = {piv, 1, 0};   // the step's pass order (3D: z, y, x; 2D: y, x)
+    for (int oi = 0; oi < 3 && st == GPE_OK; ++oi) {
+        const int a = order[oi];
+        if (oi == 1 && p->ndim != 3) continue;
         double best_ms = 1e300;
         const int ntma = (a >= 1 && !(flags & GPE_TUNE_NO_TMA)) ? 2 : 1;
         for (int var = 0; var < 2 && st == GPE_OK; ++var) {
@@ -931,7 +960,7 @@ extern "C" gpe_status gpe_plan_autotune(gpe_plan *p, const void *psi, int reps, 
                 p->use_tma[a] = ntma == 2 && ti == 0;
                 double total = 0.0;
                 for (int r = 0; r <= reps && st == GPE_OK; ++r) {   // r = 0 warms up
-                    if (psi && cudaMemcpyAsync(buf, psi, bytes, cudaMemcpyDeviceToDevice, p->st) != cudaSuccess) {
+                    if (cudaMemcpyAsync(buf, prep, bytes, cudaMemcpyDeviceToDevice, p->st) != cudaSuccess) {
                         st = fail(GPE_ECUDA, "scratch copy failed");
                         break;
                     }
@@ -953,7 +982,14 @@ extern "C" gpe_status gpe_plan_autotune(gpe_plan *p, const void *psi, int reps, 
                 }
             }
         }
+        // advance prep through this pass (with the chosen shape) for the next axis
+        if (st == GPE_OK && oi < 2) {
+            p->tile_var[a] = best.var[a];
+            p->use_tma[a] = best.tma[a];
+            st = run(p, steady_pass(p, a, prep, B));
+        }
     }
+    cudaFree(prep);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(buf);

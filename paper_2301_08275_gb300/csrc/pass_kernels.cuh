@@ -104,9 +104,10 @@ __device__ __forceinline__ void apply_phase(C (&v)[E], const R (&th)[E])
 // with the swizzled shared layout and several CTAs per SM: each lane's points
 // lie in its own row, and fewer rows per warp request with longer pieces of
 // each measured faster for complex64 rows of up to 512 points.  Rows of 256
-// or 512 points: 2 rows (shape 0; 16 points = 128 bytes of each row per warp
-// request) or 4 (shape 1) - 512^3 x pass 0.945 -> 0.895 ms; 4 beat 8 (1.27 ->
-// 1.07 ms).  Shorter complex64 rows (tiny CTAs otherwise): 4 rows (shape 0)
+// or 512 points: tiles of 512 points (shape 0: 1 row of 512 or 2 of 256, each
+// warp request reading 256 or 128 contiguous bytes of a row) or 4 rows
+// (shape 1) - 512^3 x pass with 4 / 2 / 1 rows: 0.945 / 0.892 / 0.871 ms;
+// 4 rows beat 8 (1.27 -> 1.07 ms).  Shorter complex64 rows (tiny CTAs otherwise): 4 rows (shape 0)
 // or the unsplit tile (shape 1).  Longer or complex128 rows: shape 0 is the
 // unsplit tile, shape 1 the half tile.
 template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr bool rows_split()
@@ -120,10 +121,11 @@ template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr i
     int maxpts = c64 ? 4096 : 2048, lmax = c64 ? 8 : 4;
     if (ROWS) {
         if (rows_split<R, N, ROWS, VAR>()) {
-            // complex64 rows of 256 or 512 points: 2 rows per tile (shape 0) or 4 (shape 1)
-            const bool quarter = c64 && N >= 256 && N <= 512 && VAR == 0;
-            maxpts /= quarter ? 4 : 2;
-            lmax /= quarter ? 4 : 2;
+            // complex64 rows of 256 or 512 points: tiles of 512 points (shape 0:
+            // 2 rows of 256, 1 row of 512) or 4 rows (shape 1)
+            const bool small = c64 && N >= 256 && N <= 512 && VAR == 0;
+            maxpts /= small ? 8 : 2;
+            lmax /= small ? 4 : 2;
         }
     } else if (c64 ? VAR == 0 : VAR == 1) {
         maxpts *= 2;
