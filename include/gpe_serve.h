@@ -28,7 +28,7 @@ typedef struct gpe_batch gpe_batch;
  * arrays; V_host is rejected with GPE_EUNSUPPORTED, here and by
  * gpe_serve_submit).  Instances are grouped; each group owns one plan, whose tile
  * shapes are chosen by gpe_plan_autotune on the group's grid (per-thread
- * staging; one scratch array of the group's size while the call runs).  The
+ * staging; two scratch arrays of the group's size while the call runs).  The
  * batch enqueues on cuda_stream (NULL: legacy default stream). */
 gpe_status gpe_batch_create(const gpe_plan_desc *descs, int count, void *cuda_stream, gpe_batch **out);
 gpe_status gpe_batch_destroy(gpe_batch *batch);
