@@ -4,14 +4,16 @@
  * The library advances solutions of the non-dimensional Gross-Pitaevskii
  * equation (quTARANG paper, Eq. ndGPE)
  *
- *     i dpsi/dt = -1/2 lap psi + V psi + g |psi|^2 psi,   V = 1/2 sum_a gamma_a^2 x_a^2,
+ *     i dpsi/dt = -1/2 lap psi + V psi + g |psi|^2 psi,
  *
+ * with V = 1/2 sum_a gamma_a^2 x_a^2 or any V sampled on the grid (V_host),
  * on periodic grids in 1, 2 or 3 dimensions with the TSSP scheme the paper
  * uses ("Numerical Scheme and functionalities": TSSP for dynamics, the same
  * scheme in imaginary time t -> -i t with renormalisation after every step for
  * ground states), and evaluates the norm, energy, chemical potential, rms sizes
  * (Results, item 1) and the compressible / incompressible kinetic-energy
- * spectra (feature list, item 3).
+ * spectra (feature list, item 3), completed by the quantum-pressure and
+ * particle-number spectra.
  *
  * Conventions shared by every entry point
  *   Grid      n[a] points on axis a (powers of two, 2..4096; unused axes 1),
