@@ -10,21 +10,34 @@ namespace gpe {
 // ------------------------------------------------------------------ reductions
 // sums[b*NQ + q] = sum over the lines of instance b of partials[q][line], in a
 // fixed order (strided per-thread sums, then a shared-memory tree).
-__global__ void __launch_bounds__(256) k_reduce_lines(const double *__restrict__ partials, int64_t cap, int q0,
-                                                      int64_t lpi, double *__restrict__ sums)
+__global__ void __launch_bounds__(1024) k_reduce_lines(const double *__restrict__ partials, int64_t cap, int q0,
+                                                       int64_t lpi, double *__restrict__ sums)
 {
-    __shared__ double sh[256];
+    // one block per (instance, quantity): thread t adds lines t, t + 1024, ...
+    // into four interleaved accumulators (independent loads in flight), then
+    // warp shuffles and one shared-memory stage finish the sum - every step in
+    // a fixed order, so the result does not change from run to run
+    __shared__ double sh[32];
     const int b = blockIdx.x, q = q0 + blockIdx.y, t = threadIdx.x;
     const double *p = partials + (int64_t)q * cap + (int64_t)b * lpi;
-    double s = 0.0;
-    for (int64_t j = t; j < lpi; j += 256) s += p[j];
-    sh[t] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (t < w) sh[t] += sh[t + w];
-        __syncthreads();
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int64_t j = t;
+    for (; j + 3 * 1024 < lpi; j += 4 * 1024) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] += p[j + (int64_t)k * 1024];
     }
-    if (t == 0) sums[(int64_t)b * NQ + q] = sh[0];
+    for (int k = 0; j < lpi; j += 1024, ++k) acc[k & 3] += p[j];
+    double s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((t & 31) == 0) sh[t >> 5] = s;
+    __syncthreads();
+    if (t < 32) {
+        s = sh[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (t == 0) sums[(int64_t)b * NQ + q] = s;
+    }
 }
 
 // Renormalisation of the imaginary-time step: s_b = sqrt(target / (sum rho dV)).
@@ -77,7 +90,7 @@ cudaError_t launch_reduce_lines(const double *partials, int64_t lines_cap, int n
                                 int64_t lines_per_inst, double *sums, cudaStream_t st)
 {
     dim3 grid((unsigned)batch, (unsigned)nq);
-    k_reduce_lines<<<grid, 256, 0, st>>>(partials, lines_cap, nq_first, lines_per_inst, sums);
+    k_reduce_lines<<<grid, 1024, 0, st>>>(partials, lines_cap, nq_first, lines_per_inst, sums);
     return cudaGetLastError();
 }
 
