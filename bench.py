@@ -74,7 +74,7 @@ def read_traffic(kind, key):
     vals = {}
     for line in open(path):
         if ":" in line and not line.startswith("#"):
-            k, v = line.split(":", 1)
+            k, v = line.rsplit(":", 1)      # pass kinds themselves contain ':'
             vals[k.strip()] = v.strip()
     if vals.get("source_sha") != kernel_source_hash():
         return None

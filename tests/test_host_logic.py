@@ -71,3 +71,30 @@ def test_max_over_ranks_single_process():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.max_over_ranks(3.5) == 3.5
+
+
+def test_bench_reads_the_committed_traffic_file():
+    """bench.py finds the DRAM bytes of every pass kind in profiles/traffic_tg512.txt
+    while the kernel sources are the profiled ones (kinds contain ':')."""
+    import importlib.util
+    import os
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    argv, sys.argv = sys.argv, ["bench.py"]
+    try:
+        spec.loader.exec_module(b)
+    finally:
+        sys.argv = argv
+    vals = {}
+    for line in open(os.path.join(root, "profiles", "traffic_tg512.txt")):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.rsplit(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha") != b.kernel_source_hash():
+        import pytest
+        pytest.skip("kernel sources changed since the traffic was profiled")
+    for kind in ("x512:I-NR-F", "y512:F", "y512:I", "z512:F-KR-I"):
+        t = b.read_traffic(kind, "tg512")
+        assert t is not None and 1.0e9 < t < 2.2e9, (kind, t)
