@@ -420,10 +420,43 @@ template <typename R, int N, bool ROWS, int VAR> constexpr int pass_min_blocks()
     return b < fit ? b : (fit > 0 ? fit : 1);
 }
 
-template <typename R, int N, bool ROWS, int VAR>
+// Sweep programs compiled with their slots fixed: the passes of the real- and
+// imaginary-time steps.  Program 0 reads the slots from the arguments (every
+// other sweep: first and last steps, diagnostics, spectra).
+struct SweepProg {
+    int op_pre, fft1, op_mid, fft2, op_post, red;
+};
+__host__ __device__ constexpr SweepProg sweep_prog(int p)
+{
+    return p == 1   ? SweepProg{OP_NONE, -1, OP_KREAL, 1, OP_NONE, RED_NONE}    // F, kinetic, I
+           : p == 2 ? SweepProg{OP_NONE, 1, OP_NONE, 0, OP_NONE, RED_NONE}      // I
+           : p == 3 ? SweepProg{OP_NONE, -1, OP_NONE, 0, OP_NONE, RED_NONE}     // F
+           : p == 4 ? SweepProg{OP_NONE, 1, OP_NREAL, -1, OP_NONE, RED_NONE}    // I, nonlinear, F
+           : p == 5 ? SweepProg{OP_SCALE_NIMAG, -1, OP_NONE, 0, OP_NONE, RED_NONE}   // scale, decay, F
+           : p == 6 ? SweepProg{OP_NONE, -1, OP_KIMAG, 1, OP_NONE, RED_NONE}    // F, kinetic decay, I
+           : p == 7 ? SweepProg{OP_NONE, 1, OP_NIMAG, 0, OP_NONE, RED_NORM}     // I, decay, norm
+                    : SweepProg{-1, -1, -1, -1, -1, -1};
+}
+constexpr int NUM_SWEEP_PROGS = 7;
+inline int sweep_prog_of(const PassArgs &a)
+{
+    for (int p = 1; p <= NUM_SWEEP_PROGS; ++p) {
+        const SweepProg q = sweep_prog(p);
+        if (a.op_pre == q.op_pre && a.fft1 == q.fft1 && a.op_mid == q.op_mid && a.fft2 == q.fft2 &&
+            a.op_post == q.op_post && a.red == q.red)
+            return p;
+    }
+    return 0;
+}
+
+template <typename R, int N, bool ROWS, int VAR, int PROG>
 __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_blocks<R, N, ROWS, VAR>()))
     k_pass(const PassArgs a, const __grid_constant__ CUtensorMap tmap)
 {
+    constexpr SweepProg PP = sweep_prog(PROG);
+    const int op_pre = PROG ? PP.op_pre : a.op_pre, op_mid = PROG ? PP.op_mid : a.op_mid;
+    const int op_post = PROG ? PP.op_post : a.op_post, rmode = PROG ? PP.red : a.red;
+    const int fft1 = PROG ? PP.fft1 : a.fft1, fft2 = PROG ? PP.fft2 : a.fft2;
     constexpr int LPT = lines_per_thread<R>();
     constexpr int L = pick_lines<R, N, ROWS, VAR>();
     using T = PassTile<R, N, ROWS, VAR>;
@@ -519,7 +552,7 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
 #pragma unroll
                 for (int e = 0; e < E; ++e) v[ln][e] = mk((R)0, (R)0);
 
-        if (a.red == RED_DIAG_X) {
+        if (rmode == RED_DIAG_X) {
             // real-space moments of rho = |psi|^2 along each row, then kx^2 |F_x psi|^2
             const R lox = (R)a.lo[0], hx = (R)a.h[0];
             const R *vsd = static_cast<const R *>(a.vsamp_diag);
@@ -572,7 +605,7 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
                 for (int ln = 0; ln < LPT; ++ln)
                     if (tl == 0 && g[ln].valid) a.partials[(int64_t)k * a.lines_cap + g[ln].lg] = q[k][ln];
             }
-        } else if (a.red == RED_DIAG_K) {
+        } else if (rmode == RED_DIAG_K) {
             T::template fft<-1>(v, sm, tl, l0, tw);
             const R kf = (R)a.kf[a.axis];
             double sk[LPT];
@@ -594,18 +627,18 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
         } else {
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln)
-                point_op<R, E, TPL>(a.op_pre, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
-            if (a.fft1 < 0) T::template fft<-1>(v, sm, tl, l0, tw);
-            else if (a.fft1 > 0) T::template fft<1>(v, sm, tl, l0, tw);
+                point_op<R, E, TPL>(op_pre, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
+            if (fft1 < 0) T::template fft<-1>(v, sm, tl, l0, tw);
+            else if (fft1 > 0) T::template fft<1>(v, sm, tl, l0, tw);
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln)
-                point_op<R, E, TPL>(a.op_mid, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
-            if (a.fft2 < 0) T::template fft<-1>(v, sm, tl, l0, tw);
-            else if (a.fft2 > 0) T::template fft<1>(v, sm, tl, l0, tw);
+                point_op<R, E, TPL>(op_mid, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
+            if (fft2 < 0) T::template fft<-1>(v, sm, tl, l0, tw);
+            else if (fft2 > 0) T::template fft<1>(v, sm, tl, l0, tw);
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln)
-                point_op<R, E, TPL>(a.op_post, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
-            if (a.red == RED_NORM) {
+                point_op<R, E, TPL>(op_post, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
+            if (rmode == RED_NORM) {
                 double sn[LPT];
 #pragma unroll
                 for (int ln = 0; ln < LPT; ++ln) {
@@ -786,8 +819,8 @@ static cudaError_t prepare(K kern, LaunchCache &lc, int nt, size_t smem, int *ca
     return cudaSuccess;
 }
 
-template <typename R, int N, bool ROWS, int VAR>
-static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap)
+template <typename R, int N, bool ROWS, int VAR, int PROG>
+static cudaError_t launch_pass_p(const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap)
 {
     constexpr int L = pick_lines<R, N, ROWS, VAR>();
     using T = PassTile<R, N, ROWS, VAR>;
@@ -798,12 +831,37 @@ static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st, const CUten
                              a.axis < 1 || a.o0n % L != 0))
         return cudaErrorInvalidValue;
     int cap = 0;
-    cudaError_t e = prepare(k_pass<R, N, ROWS, VAR>, lc, T::NT, smem, &cap);
+    cudaError_t e = prepare(k_pass<R, N, ROWS, VAR, PROG>, lc, T::NT, smem, &cap);
     if (e != cudaSuccess) return e;
     if (a.ntiles <= 0) return cudaSuccess;
     const int grid = (int)(a.ntiles < cap ? a.ntiles : cap);
-    k_pass<R, N, ROWS, VAR><<<grid, T::NT, smem, st>>>(a, tmap ? *tmap : none);
+    k_pass<R, N, ROWS, VAR, PROG><<<grid, T::NT, smem, st>>>(a, tmap ? *tmap : none);
     return cudaGetLastError();
+}
+
+// complex64 lines of 256 to 1024 points (the large grids) get the fixed-program
+// kernels of the sweeps they run; everything else the generic one
+template <typename R, int N, bool ROWS> constexpr bool sweep_progs_compiled()
+{
+    return sizeof(R) == 4 && N >= 256 && N <= 1024;
+}
+template <typename R, int N, bool ROWS, int VAR>
+static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap)
+{
+    if constexpr (sweep_progs_compiled<R, N, ROWS>()) {
+        const int p = sweep_prog_of(a);
+        if constexpr (ROWS) {
+            if (p == 4) return launch_pass_p<R, N, ROWS, VAR, 4>(a, st, tmap);
+            if (p == 5) return launch_pass_p<R, N, ROWS, VAR, 5>(a, st, tmap);
+            if (p == 7) return launch_pass_p<R, N, ROWS, VAR, 7>(a, st, tmap);
+        } else {
+            if (p == 1) return launch_pass_p<R, N, ROWS, VAR, 1>(a, st, tmap);
+            if (p == 2) return launch_pass_p<R, N, ROWS, VAR, 2>(a, st, tmap);
+            if (p == 3) return launch_pass_p<R, N, ROWS, VAR, 3>(a, st, tmap);
+            if (p == 6) return launch_pass_p<R, N, ROWS, VAR, 6>(a, st, tmap);
+        }
+    }
+    return launch_pass_p<R, N, ROWS, VAR, 0>(a, st, tmap);
 }
 
 static int sm_count()
