@@ -306,15 +306,30 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
         return i * L + l;
     }
 
-    __device__ __forceinline__ static void ld(const C *sm, int i, int l0, C (&v)[LPT][E], int e)
+    // index of a thread's own point tl + TPL*e.  When TPL is a multiple of QS
+    // and of the first radix, the swizzle key of i depends on tl and on e only
+    // through a constant, and XOR-ing it leaves TPL*e untouched: the index is
+    // (tl ^ key) + TPL*e, a per-thread base plus a constant (same value as sidx).
+    __device__ __forceinline__ static int sidx_own(int tl, int e, int l)
     {
+        if constexpr (SW && TPL % QS == 0 && TPL % (1 << SWS) == 0) {
+            const int key = ((tl >> SWS) + (TPL >> SWS) * e) & (QS - 1);
+            return ((tl ^ key) + TPL * e) * L + l;
+        } else {
+            return sidx(tl + TPL * e, l);
+        }
+    }
+
+    __device__ __forceinline__ static void ld(const C *sm, int tl, int e, int l0, C (&v)[LPT][E])
+    {
+        const int i0 = sidx_own(tl, e, l0);
         if constexpr (LPT == 2 && sizeof(C) == 8) {
-            const float4 q = *reinterpret_cast<const float4 *>(sm + sidx(i, l0));
+            const float4 q = *reinterpret_cast<const float4 *>(sm + i0);
             v[0][e] = mk(q.x, q.y);
             v[1][e] = mk(q.z, q.w);
         } else {
 #pragma unroll
-            for (int ln = 0; ln < LPT; ++ln) v[ln][e] = sm[sidx(i, l0 + ln)];
+            for (int ln = 0; ln < LPT; ++ln) v[ln][e] = sm[i0 + ln];
         }
     }
     __device__ __forceinline__ static void st(C *sm, int i, int l0, const C *x)
@@ -356,19 +371,32 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
         }
     }
 
-    template <int DIR, int p>
-    __device__ __forceinline__ static void pass(C (&v)[LPT][E], C *sm, int tl, int l0, const U *__restrict__ tw)
+    // Shared-memory regions of the passes.  Without PING every non-final pass
+    // writes the tile buffer sb, after a barrier that follows all reads of the
+    // previous pass (two barriers per pass).  With PING the outputs alternate
+    // between a scratch region ss (even passes) and sb (odd passes): the region
+    // a pass writes was last read one pass earlier, before the barrier that
+    // opens the pass, so one barrier per pass suffices.  Pass 0 then needs none
+    // when the pass count is odd: the previous transform (or tile) last read ss
+    // in a pass that a later barrier closed.  A transform's input registers
+    // must not depend on pending reads of ss or sb by other threads beyond
+    // these rules (the tile's own load from sb is closed by the barrier of pass 1).
+    template <int DIR, int p, bool PING = false>
+    __device__ __forceinline__ static void pass(C (&v)[LPT][E], C *sb, C *ss, int tl, int l0,
+                                                const U *__restrict__ tw)
     {
         constexpr int r = Radix<N>::radix(p);
         constexpr int Ns = Radix<N>::ns(p);
         constexpr int B = E / r;
         constexpr bool last = (p == Radix<N>::P - 1);
+        C *const rd = (PING && p % 2 == 1) ? ss : sb;    // written by pass p-1
+        C *const wr = (PING && p % 2 == 0) ? ss : sb;
         if constexpr (p > 0) {
             __syncthreads();
 #pragma unroll
-            for (int e = 0; e < E; ++e) ld(sm, tl + TPL * e, l0, v, e);
-            if constexpr (!last) __syncthreads();
-        } else if constexpr (!last) {
+            for (int e = 0; e < E; ++e) ld(rd, tl, e, l0, v);
+            if constexpr (!last && !PING) __syncthreads();
+        } else if constexpr (!last && (!PING || Radix<N>::P % 2 == 0)) {
             __syncthreads();
         }
 #pragma unroll
@@ -403,18 +431,18 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
                     C y[LPT];
 #pragma unroll
                     for (int ln = 0; ln < LPT; ++ln) y[ln] = x[ln][m];
-                    st(sm, base + m * Ns, l0, y);
+                    st(wr, base + m * Ns, l0, y);
                 }
             }
         }
     }
 
-    template <int DIR, int p = 0>
-    __device__ __forceinline__ static void fft(C (&v)[LPT][E], C *sm, int tl, int l0, const U *tw)
+    template <int DIR, bool PING = false, int p = 0>
+    __device__ __forceinline__ static void fft(C (&v)[LPT][E], C *sb, C *ss, int tl, int l0, const U *tw)
     {
         if constexpr (p < Radix<N>::P) {
-            pass<DIR, p>(v, sm, tl, l0, tw);
-            fft<DIR, p + 1>(v, sm, tl, l0, tw);
+            pass<DIR, p, PING>(v, sb, ss, tl, l0, tw);
+            fft<DIR, PING, p + 1>(v, sb, ss, tl, l0, tw);
         }
     }
 };

@@ -400,9 +400,9 @@ template <typename R, int N, bool ROWS, int VAR>
 using PassTile = GTile<R, N, pick_lines<R, N, ROWS, VAR>(), lines_per_thread<R>(), rows_split<R, N, ROWS, VAR>(),
                        pass_points_per_thread<R, N, ROWS>()>;
 
-// dynamic shared memory of one CTA: two staging buffers, per-line reduction
-// scratch, twiddles, two mbarriers
-template <typename R, int N, bool ROWS, int VAR> constexpr size_t pass_smem_bytes()
+// dynamic shared memory of one CTA without the transform scratch: two staging
+// buffers, per-line reduction scratch, twiddles, two mbarriers
+template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr size_t pass_smem_base()
 {
     using T = PassTile<R, N, ROWS, VAR>;
     return 2 * sizeof(typename T::C) * T::SMEM_POINTS + sizeof(double) * (size_t)(T::SMEM_POINTS / T::E) +
@@ -411,13 +411,30 @@ template <typename R, int N, bool ROWS, int VAR> constexpr size_t pass_smem_byte
 // CTAs per SM the registers are budgeted for: 4 per SM for split rows (1024 /
 // threads per CTA, at most 16), else 2 (1 for CTAs of more than 512 threads),
 // never more than fit in the SM's shared memory
-template <typename R, int N, bool ROWS, int VAR> constexpr int pass_min_blocks()
+template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr int pass_min_blocks()
 {
     constexpr int nt = PassTile<R, N, ROWS, VAR>::NT;
     constexpr int want = 1024 / nt > 16 ? 16 : 1024 / nt;
     constexpr int b = rows_split<R, N, ROWS, VAR>() && want > 2 ? want : (nt > 512 ? 1 : 2);
-    constexpr int fit = (int)(227 * 1024 / (pass_smem_bytes<R, N, ROWS, VAR>() + 1024));
+    constexpr int fit = (int)(227 * 1024 / (pass_smem_base<R, N, ROWS, VAR>() + 1024));
     return b < fit ? b : (fit > 0 ? fit : 1);
+}
+// A third tile-sized region lets the transform passes alternate between two
+// regions (one barrier per pass instead of two).  It is added to kernels built
+// for one CTA per SM, whose shared memory is otherwise partly idle, where it
+// fits: 512^3 complex64 z sweep 0.810 -> 0.797 ms; with two CTAs per SM the y
+// sweep slowed (0.411 -> 0.433 ms).
+template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr bool pass_ping()
+{
+    using T = PassTile<R, N, ROWS, VAR>;
+    constexpr size_t with = pass_smem_base<R, N, ROWS, VAR>() + sizeof(typename T::C) * T::SMEM_POINTS;
+    return Radix<N>::P > 1 && pass_min_blocks<R, N, ROWS, VAR>() == 1 && with + 1024 <= 227 * 1024;
+}
+template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr size_t pass_smem_bytes()
+{
+    using T = PassTile<R, N, ROWS, VAR>;
+    return pass_smem_base<R, N, ROWS, VAR>() +
+           (pass_ping<R, N, ROWS, VAR>() ? sizeof(typename T::C) * T::SMEM_POINTS : 0);
 }
 
 // Sweep programs compiled with their slots fixed: the passes of the real- and
@@ -463,13 +480,15 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
     using C = typename T::C;
     using U = typename T::U;
     constexpr int E = T::E, TPL = T::TPL;
+    constexpr bool PING = pass_ping<R, N, ROWS, VAR>();
     extern __shared__ __align__(128) unsigned char smraw[];
     C *buf0 = reinterpret_cast<C *>(smraw);
     C *buf1 = buf0 + T::SMEM_POINTS;
-    double *red = reinterpret_cast<double *>(smraw + 2 * sizeof(C) * T::SMEM_POINTS);
-    U *tw = reinterpret_cast<U *>(smraw + 2 * sizeof(C) * T::SMEM_POINTS + sizeof(double) * N * L / E);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smraw + 2 * sizeof(C) * T::SMEM_POINTS +
-                                                  sizeof(double) * N * L / E + sizeof(U) * N);
+    constexpr size_t tiles_bytes = (PING ? 3 : 2) * sizeof(C) * T::SMEM_POINTS;
+    C *const scr = PING ? buf1 + T::SMEM_POINTS : nullptr;
+    double *red = reinterpret_cast<double *>(smraw + tiles_bytes);
+    U *tw = reinterpret_cast<U *>(smraw + tiles_bytes + sizeof(double) * N * L / E);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smraw + tiles_bytes + sizeof(double) * N * L / E + sizeof(U) * N);
     const int t = threadIdx.x, l0 = (t % T::NP) * LPT, tl = t / T::NP;
     T::load_twiddles(tw, static_cast<const U *>(a.tw), t, T::NT);
 
@@ -515,7 +534,7 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
                     const C *src = inst_src<C>(a, g.inst) + g.off;
 #pragma unroll
                     for (int e = 0; e < E; ++e)
-                        cp_async_point(buf + T::sidx(tl + TPL * e, l0 + ln), src + (int64_t)(tl + TPL * e) * a.estride);
+                        cp_async_point(buf + T::sidx_own(tl, e, l0 + ln), src + (int64_t)(tl + TPL * e) * a.estride);
                 }
             }
         }
@@ -545,7 +564,7 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
         for (int ln = 0; ln < LPT; ++ln) g[ln] = line_geom<L>(a, tile, l0 + ln);
         C v[LPT][E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) T::ld(sm, tl + TPL * e, l0, v, e);
+        for (int e = 0; e < E; ++e) T::ld(sm, tl, e, l0, v);
 #pragma unroll
         for (int ln = 0; ln < LPT; ++ln)
             if (!g[ln].valid)
@@ -570,7 +589,7 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
                     if (vsd) sv[ln] += vsd[g[ln].off + (int64_t)(tl + TPL * e) * a.estride] * rho;
                 }
             }
-            T::template fft<-1>(v, sm, tl, l0, tw);
+            T::template fft<-1, PING>(v, sm, PING ? scr : sm, tl, l0, tw);
             const R kf = (R)a.kf[0];
             R sk[LPT];
 #pragma unroll
@@ -606,7 +625,7 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
                     if (tl == 0 && g[ln].valid) a.partials[(int64_t)k * a.lines_cap + g[ln].lg] = q[k][ln];
             }
         } else if (rmode == RED_DIAG_K) {
-            T::template fft<-1>(v, sm, tl, l0, tw);
+            T::template fft<-1, PING>(v, sm, PING ? scr : sm, tl, l0, tw);
             const R kf = (R)a.kf[a.axis];
             double sk[LPT];
 #pragma unroll
@@ -628,13 +647,13 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln)
                 point_op<R, E, TPL>(op_pre, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
-            if (fft1 < 0) T::template fft<-1>(v, sm, tl, l0, tw);
-            else if (fft1 > 0) T::template fft<1>(v, sm, tl, l0, tw);
+            if (fft1 < 0) T::template fft<-1, PING>(v, sm, PING ? scr : sm, tl, l0, tw);
+            else if (fft1 > 0) T::template fft<1, PING>(v, sm, PING ? scr : sm, tl, l0, tw);
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln)
                 point_op<R, E, TPL>(op_mid, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
-            if (fft2 < 0) T::template fft<-1>(v, sm, tl, l0, tw);
-            else if (fft2 > 0) T::template fft<1>(v, sm, tl, l0, tw);
+            if (fft2 < 0) T::template fft<-1, PING>(v, sm, PING ? scr : sm, tl, l0, tw);
+            else if (fft2 > 0) T::template fft<1, PING>(v, sm, PING ? scr : sm, tl, l0, tw);
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln)
                 point_op<R, E, TPL>(op_post, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
