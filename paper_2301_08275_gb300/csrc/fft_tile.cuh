@@ -332,13 +332,24 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
             for (int ln = 0; ln < LPT; ++ln) v[ln][e] = sm[i0 + ln];
         }
     }
-    __device__ __forceinline__ static void st(C *sm, int i, int l0, const C *x)
+    // swizzled point index before the line interleave
+    __host__ __device__ static constexpr int sraw(int i) { return SW ? (i ^ ((i >> SWS) & (QS - 1))) : i; }
+    // Index of Stockham output base + m*Ns of a pass.  base and m*Ns occupy
+    // disjoint bits (base = (j div Ns) Ns r + k with k < Ns, m < r), so do their
+    // shifted copies, and the swizzle is linear over XOR on such pairs:
+    // sraw(base + m Ns) = sraw(base) ^ sraw(m Ns), the second a constant.
+    template <int Ns> __device__ __forceinline__ static int sidx_out(int sb, int m, int l)
+    {
+        if constexpr (SW) return (sb ^ sraw(m * Ns)) * L + l;
+        return (sb + m * Ns) * L + l;
+    }
+    __device__ __forceinline__ static void st_at(C *sm, int i0, const C *x)
     {
         if constexpr (LPT == 2 && sizeof(C) == 8) {
-            *reinterpret_cast<float4 *>(sm + sidx(i, l0)) = make_float4(x[0].x, x[0].y, x[1].x, x[1].y);
+            *reinterpret_cast<float4 *>(sm + i0) = make_float4(x[0].x, x[0].y, x[1].x, x[1].y);
         } else {
 #pragma unroll
-            for (int ln = 0; ln < LPT; ++ln) sm[sidx(i, l0 + ln)] = x[ln];
+            for (int ln = 0; ln < LPT; ++ln) sm[i0 + ln] = x[ln];
         }
     }
 
@@ -426,12 +437,13 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
                     for (int m = 0; m < r; ++m) v[ln][q + m * B] = x[ln][m];
             } else {
                 const int base = (j / Ns) * Ns * r + k;
+                const int sb = SW ? sraw(base) : base;
 #pragma unroll
                 for (int m = 0; m < r; ++m) {
                     C y[LPT];
 #pragma unroll
                     for (int ln = 0; ln < LPT; ++ln) y[ln] = x[ln][m];
-                    st(wr, base + m * Ns, l0, y);
+                    st_at(wr, sidx_out<Ns>(sb, m, l0), y);
                 }
             }
         }
