@@ -300,7 +300,7 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
 
     static constexpr int QS = 128 / (L * (int)sizeof(C)) > 1 ? 128 / (L * (int)sizeof(C)) : 1;
     static constexpr int SWS = ilog2c(Radix<N>::radix(0));
-    __device__ __forceinline__ static int sidx(int i, int l)
+    __host__ __device__ __forceinline__ static int sidx(int i, int l)
     {
         if constexpr (SW) return (i ^ ((i >> SWS) & (QS - 1))) * L + l;
         return i * L + l;
@@ -310,7 +310,7 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
     // and of the first radix, the swizzle key of i depends on tl and on e only
     // through a constant, and XOR-ing it leaves TPL*e untouched: the index is
     // (tl ^ key) + TPL*e, a per-thread base plus a constant (same value as sidx).
-    __device__ __forceinline__ static int sidx_own(int tl, int e, int l)
+    __host__ __device__ __forceinline__ static int sidx_own(int tl, int e, int l)
     {
         if constexpr (SW && TPL % QS == 0 && TPL % (1 << SWS) == 0) {
             const int key = ((tl >> SWS) + (TPL >> SWS) * e) & (QS - 1);
@@ -338,7 +338,7 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
     // disjoint bits (base = (j div Ns) Ns r + k with k < Ns, m < r), so do their
     // shifted copies, and the swizzle is linear over XOR on such pairs:
     // sraw(base + m Ns) = sraw(base) ^ sraw(m Ns), the second a constant.
-    template <int Ns> __device__ __forceinline__ static int sidx_out(int sb, int m, int l)
+    template <int Ns> __host__ __device__ __forceinline__ static int sidx_out(int sb, int m, int l)
     {
         if constexpr (SW) return (sb ^ sraw(m * Ns)) * L + l;
         return (sb + m * Ns) * L + l;
