@@ -106,8 +106,8 @@ __device__ __forceinline__ void apply_phase(C (&v)[E], const R (&th)[E])
 // each measured faster for complex64 rows of up to 512 points.  Rows of 256
 // or 512 points: tiles of 512 points (shape 0: 1 row of 512 or 2 of 256, each
 // warp request reading 256 or 128 contiguous bytes of a row) or 4 rows
-// (shape 1) - 512^3 x pass with 4 / 2 / 1 rows: 0.945 / 0.892 / 0.871 ms;
-// 4 rows beat 8 (1.27 -> 1.07 ms).  Shorter complex64 rows (tiny CTAs otherwise): 4 rows (shape 0)
+// (shape 1) - 512^3 x pass with 4 / 2 / 1 rows: 0.839 / 0.716 / 0.705 ms
+// (fixed-program kernels; 4 rows beat 8 in earlier builds, 1.27 -> 1.07 ms).  Shorter complex64 rows (tiny CTAs otherwise): 4 rows (shape 0)
 // or the unsplit tile (shape 1).  Longer or complex128 rows: shape 0 is the
 // unsplit tile, shape 1 the half tile.
 template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr bool rows_split()
