@@ -157,6 +157,15 @@ gpe_status gpe_spectrum(gpe_plan *plan, const void *psi_dev, unsigned kinds, dou
  *   GPE_OPT_TILE_X/Y/Z   tile shape of the sweeps along x, y, z (0 default,
  *                        1 the alternative compiled shape: different lines per
  *                        tile and CTAs per SM).
+ *   GPE_OPT_GENERIC_PASSES  1: every sweep runs the generic pass kernel, which
+ *                        reads its program (pointwise ops, transforms,
+ *                        reduction) from the launch arguments; 0 (default):
+ *                        the sweeps of the real- and imaginary-time steps on
+ *                        complex64 lines of 256 to 1024 points run kernels
+ *                        compiled for their program.  For tests and timing.
+ *                        The one exception to bit-identical results: with
+ *                        this option imaginary-time steps can differ in the
+ *                        last place (real-time steps do not).
  *   GPE_OPT_TEST_STALL_COPIES  test hook for the failure handling: 1 makes
  *                        every copy-engine tile wait expect 16 bytes more than
  *                        its copies deliver, so the wait runs out after its
@@ -172,6 +181,7 @@ enum gpe_option {
     GPE_OPT_TILE_Z = 4,
     GPE_OPT_TMA_Y = 5,
     GPE_OPT_TMA_Z = 6,
+    GPE_OPT_GENERIC_PASSES = 7,
     GPE_OPT_TEST_STALL_COPIES = 99
 };
 gpe_status gpe_plan_set_option(gpe_plan *plan, int option, int64_t value);

@@ -120,6 +120,7 @@ struct gpe_plan {
     bool use_tma[3] = {true, true, true};   // copy-engine staging per axis (strided axes only)
     int tile_var[3] = {0, 0, 0};            // tile shape per axis
     int tx_extra = 0;                       // GPE_OPT_TEST_STALL_COPIES
+    bool generic_passes = false;            // GPE_OPT_GENERIC_PASSES
 };
 
 static gpe_status check_err(gpe_plan *p);
@@ -649,6 +650,7 @@ static gpe_status run(gpe_plan *p, const PassArgs &a_in)
 {
     PassArgs a = a_in;
     a.err = p->err;
+    a.generic = p->generic_passes ? 1 : 0;
     const CUtensorMap *tm = nullptr;
     // strided sweeps over one array of back-to-back instances, with whole
     // tiles of consecutive x lines, take the copy-engine staging
@@ -828,6 +830,10 @@ extern "C" gpe_status gpe_plan_set_option(gpe_plan *p, int option, int64_t value
         p->use_tma[option - GPE_OPT_TMA_Y + 1] = value != 0;
         return GPE_OK;
     }
+    if (option == GPE_OPT_GENERIC_PASSES) {
+        p->generic_passes = value != 0;
+        return GPE_OK;
+    }
     return fail(GPE_EINVAL, "unknown plan option");
 }
 
@@ -838,6 +844,7 @@ extern "C" gpe_status gpe_plan_get_option(const gpe_plan *p, int option, int64_t
     else if (option >= GPE_OPT_TILE_X && option <= GPE_OPT_TILE_Z) *value = p->tile_var[option - GPE_OPT_TILE_X];
     else if (option == GPE_OPT_TMA_Y || option == GPE_OPT_TMA_Z) *value = p->use_tma[option - GPE_OPT_TMA_Y + 1] ? 1 : 0;
     else if (option == GPE_OPT_TEST_STALL_COPIES) *value = p->tx_extra ? 1 : 0;
+    else if (option == GPE_OPT_GENERIC_PASSES) *value = p->generic_passes ? 1 : 0;
     else return fail(GPE_EINVAL, "unknown plan option");
     return GPE_OK;
 }

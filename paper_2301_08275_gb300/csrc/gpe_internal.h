@@ -77,6 +77,7 @@ struct PassArgs {
     int tx_extra;          // bytes added to each tile's expected count (0; > 0 only in the
                            // failure-handling test, so that the wait runs out)
     int *err;              // device error word (bit ERR_TMA_TIMEOUT), may be NULL
+    int generic;           // host side: 1 launches the generic kernel whatever the program
 };
 
 enum : int {

@@ -438,8 +438,12 @@ template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr s
 }
 
 // Sweep programs compiled with their slots fixed: the passes of the real- and
-// imaginary-time steps.  Program 0 reads the slots from the arguments (every
-// other sweep: first and last steps, diagnostics, spectra).
+// imaginary-time steps, with the first and last x sweeps of a real-time call.
+// Program 0 reads the slots from the arguments (every other sweep:
+// diagnostics, spectra, the final renormalisation).  The real-time programs
+// give the generic kernel's bits (tested); the imaginary-time ones (5-7) can
+// round differently from it in the last place (seen on the decay sweeps, cause
+// not identified), well inside the parity tolerances.
 struct SweepProg {
     int op_pre, fft1, op_mid, fft2, op_post, red;
 };
@@ -452,11 +456,14 @@ __host__ __device__ constexpr SweepProg sweep_prog(int p)
            : p == 5 ? SweepProg{OP_SCALE_NIMAG, -1, OP_NONE, 0, OP_NONE, RED_NONE}   // scale, decay, F
            : p == 6 ? SweepProg{OP_NONE, -1, OP_KIMAG, 1, OP_NONE, RED_NONE}    // F, kinetic decay, I
            : p == 7 ? SweepProg{OP_NONE, 1, OP_NIMAG, 0, OP_NONE, RED_NORM}     // I, decay, norm
+           : p == 8 ? SweepProg{OP_NREAL, -1, OP_NONE, 0, OP_NONE, RED_NONE}    // first half-step, F
+           : p == 9 ? SweepProg{OP_NONE, 1, OP_NREAL, 0, OP_NONE, RED_NONE}     // I, last half-step
                     : SweepProg{-1, -1, -1, -1, -1, -1};
 }
-constexpr int NUM_SWEEP_PROGS = 7;
+constexpr int NUM_SWEEP_PROGS = 9;
 inline int sweep_prog_of(const PassArgs &a)
 {
+    if (a.generic) return 0;
     for (int p = 1; p <= NUM_SWEEP_PROGS; ++p) {
         const SweepProg q = sweep_prog(p);
         if (a.op_pre == q.op_pre && a.fft1 == q.fft1 && a.op_mid == q.op_mid && a.fft2 == q.fft2 &&
@@ -873,6 +880,8 @@ static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st, const CUten
             if (p == 4) return launch_pass_p<R, N, ROWS, VAR, 4>(a, st, tmap);
             if (p == 5) return launch_pass_p<R, N, ROWS, VAR, 5>(a, st, tmap);
             if (p == 7) return launch_pass_p<R, N, ROWS, VAR, 7>(a, st, tmap);
+            if (p == 8) return launch_pass_p<R, N, ROWS, VAR, 8>(a, st, tmap);
+            if (p == 9) return launch_pass_p<R, N, ROWS, VAR, 9>(a, st, tmap);
         } else {
             if (p == 1) return launch_pass_p<R, N, ROWS, VAR, 1>(a, st, tmap);
             if (p == 2) return launch_pass_p<R, N, ROWS, VAR, 2>(a, st, tmap);

@@ -386,6 +386,38 @@ def test_tile_shapes_and_autotuner_keep_results_bit_identical(gpe, n, prec):
         assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])
 
 
+@pytest.mark.parametrize("n", [(512, 256, 16), (256, 1024), (1024, 16, 256)], ids=lambda n: "x".join(map(str, n)))
+def test_fixed_program_kernels_match_the_generic_kernel(gpe, n):
+    """Sweeps with their program compiled in (complex64 lines of 256 to 1024
+    points) against the generic kernel that reads the program from its
+    arguments, in both tile shapes, with a trap: real-time steps give the same
+    bits; imaginary-time steps agree to a few units in the last place (the
+    decay sweeps' compiled instances may round differently)."""
+    import torch
+    sp = _spec(n)
+    psi0 = gi.random_field(sp, seed=31, smooth=0.05).astype(np.complex64)
+    outs = []
+    for generic in (0, 1):
+        for shape in (0, 1):
+            p = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma[: sp.ndim], prec=gpe.GPE_C64)
+            p.set_option(gpe.GPE_OPT_GENERIC_PASSES, generic)
+            assert p.get_option(gpe.GPE_OPT_GENERIC_PASSES) == generic
+            for opt in (gpe.GPE_OPT_TILE_X, gpe.GPE_OPT_TILE_Y, gpe.GPE_OPT_TILE_Z):
+                p.set_option(opt, shape)
+            x = torch.from_numpy(psi0.copy()).cuda()
+            p.step_real(x, 4)
+            y = torch.from_numpy(psi0.copy()).cuda()
+            p.step_imag(y, 3, etol=0.0, check_every=3)
+            torch.cuda.synchronize()
+            outs.append((x.cpu().numpy(), y.cpu().numpy()))
+            p.close()
+    assert np.isfinite(outs[0][0]).all() and np.abs(outs[0][0]).max() > 0
+    scale = np.abs(outs[0][1]).max()
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0])
+        assert np.abs(o[1] - outs[0][1]).max() <= 1e-6 * scale
+
+
 def test_plan_options_reject_bad_values(gpe):
     sp = _spec((32, 16))
     p = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma[: sp.ndim], prec=gpe.GPE_C64)
