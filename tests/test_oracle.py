@@ -181,6 +181,51 @@ def test_ground_state_g0_is_the_oscillator_gaussian(orc, spec):
         assert abs(r[a] - s) / s < 2e-6
 
 
+def test_convergence_test_stops_by_its_rule(orc):
+    """Convergence test (imaginary time): after every check_every steps (the
+    last chunk cut at max_steps) the energy is compared with the previous
+    check, the input's energy serving as the first; the run stops at the first
+    change below etol and reports that check's energy.  Checked against the
+    rule stepped by hand with the oracle's own step and energy: a loose etol
+    stops at the first check, etol = 0 runs max_steps (with a partial last
+    chunk), and a mid-range etol stops where the hand-run first meets it."""
+    sp = gi.Spec(n=(64, 32), lo=(-8, -6), length=(16, 12), g=20.0, dt=2e-3, gamma=(1.0, 1.5))
+    P = orc.Problem(**sp.kwargs())
+    psi0 = gi.harmonic_gaussian(gi.Spec(n=sp.n, lo=sp.lo, length=sp.length, gamma=(0.5, 0.5)))
+
+    def by_hand(max_steps, etol, every):
+        y = psi0.astype(np.complex128)
+        eprev = P.norm_energy(y)[4]
+        done = 0
+        while done < max_steps:
+            chunk = min(every, max_steps - done)
+            y = P.step_imag(y, chunk)
+            done += chunk
+            e = P.norm_energy(y)[4]
+            if abs(e - eprev) < etol:
+                return y, done, e
+            eprev = e
+        return y, done, eprev
+
+    # loose tolerance: the first check already meets it
+    psi, steps, E = P.ground(psi0, max_steps=1000, etol=1e3, check_every=7)
+    assert steps == 7
+    # etol = 0 never stops early; 23 = 3 * 7 + 2 leaves a 2-step last chunk
+    psi, steps, E = P.ground(psi0, max_steps=23, etol=0.0, check_every=7)
+    ref, rsteps, rE = by_hand(23, 0.0, 7)
+    assert steps == 23 == rsteps and E == rE and np.array_equal(psi, ref)
+    assert E == P.norm_energy(psi)[4]
+    # a tolerance met part-way: the same stopping check as the hand-run, and
+    # the energy change there is below etol while the one before is not
+    psi, steps, E = P.ground(psi0, max_steps=5000, etol=1e-6, check_every=10)
+    ref, rsteps, rE = by_hand(5000, 1e-6, 10)
+    assert 10 < steps < 5000 and steps == rsteps and E == rE and np.array_equal(psi, ref)
+    e_before = P.norm_energy(P.step_imag(psi0.astype(np.complex128), steps - 10))[4]
+    assert abs(E - e_before) < 1e-6
+    e_two_before = P.norm_energy(P.step_imag(psi0.astype(np.complex128), steps - 20))[4]
+    assert abs(e_before - e_two_before) >= 1e-6
+
+
 def test_table1_2d_ground_states(orc):
     """2D rows of the paper's Table 1 (r_rms and mu of the ground state in
     V=(x^2+y^2)/2 from psi0 = pi^-1/2 e^{-r^2/2}).  128^2 on [-10,10)^2 at
