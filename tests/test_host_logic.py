@@ -98,3 +98,24 @@ def test_bench_reads_the_committed_traffic_file():
     for kind in ("x512:I-NR-F", "y512:F", "y512:I", "z512:F-KR-I"):
         t = b.read_traffic(kind, "tg512")
         assert t is not None and 1.0e9 < t < 2.2e9, (kind, t)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the FP64 oracle on the host cores) prints one
+    JSON line with the metric and unit of the GPU arm, impl=reference, a
+    cpu_baseline describing the run and an e2e entry without transfers."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"] == "TSSP grid-point updates/s vs HBM roofline" and d["unit"] == "grid-point updates/s"
+    assert d["higher_is_better"] is True and d["value"] > 0 and d["warmup"] >= 3 and d["steps"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("3D Taylor-Green 512^3")
