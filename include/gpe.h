@@ -147,7 +147,8 @@ gpe_status gpe_spectrum(gpe_plan *plan, const void *psi_dev, unsigned kinds, dou
 
 /* Plan options (implementation choices, no counterpart in the paper).  Every
  * option takes 0 or 1; results are bit-identical for every setting (each
- * line's arithmetic does not depend on them), only the speed changes.
+ * line's arithmetic does not depend on them, with the one exception noted at
+ * GPE_OPT_GENERIC_PASSES), only the speed changes.
  *   GPE_OPT_TMA_STAGING  1 (default): tiles of the y and z sweeps are fetched
  *                        by the tensor-memory accelerator when the grid allows
  *                        it (n0 a multiple of the tile's line count, instances
