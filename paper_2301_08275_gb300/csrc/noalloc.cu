@@ -10,13 +10,13 @@
 //
 // The array is a file-scope __device__ variable, so every GPU that loads this
 // library holds it (about 2.4 MiB) until the process exits.  In host code its
-// name is only a stand-in for the device symbol, never a usable address: the
-// device address is obtained once per device with cudaGetSymbolAddress (on
-// the first call made with that device current) and passed to the kernels.
+// name is only a stand-in for the device symbol, never a usable address: every
+// call looks up the device address on the current device with
+// cudaGetSymbolAddress and passes it to the kernels.  The lookup allocates
+// nothing once the module is loaded and is not cached, so a device reset or a
+// new primary context between calls leaves no stale address behind.
 #include <math.h>
 #include <string.h>
-
-#include <mutex>
 
 #include "../../include/gpe.h"
 #include "fft_tile.cuh"
@@ -41,9 +41,6 @@ constexpr size_t kScratchBytes = kOutOff + 256;
 static_assert(kTwOff % 256 == 0 && kParamOff % 256 == 0, "scratch regions must stay aligned");
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
-
-std::mutex g_mu;
-void *g_dev_ptr[64] = {nullptr};
 
 gpe_status nfail(gpe_status s, const char *msg)
 {
@@ -176,20 +173,13 @@ extern "C" gpe_status gpe_norm_energy_noalloc(const gpe_plan_desc *d, const void
             return nfail(GPE_EUNSUPPORTED, "grid too large for the static scratch: N / n[a] must be <= "
                                            "GPE_NOALLOC_MAX_LINES (32768) on every axis");
 
-    int dev = -1;
-    NA_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return nfail(GPE_EINVAL, "device index out of range");
-    unsigned char *base = nullptr;
+    // the array's address on the current device, looked up on every call
+    void *sym = nullptr;
     {
-        std::lock_guard<std::mutex> g(g_mu);
-        if (!g_dev_ptr[dev]) {
-            void *p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || !p) return nfail(GPE_ECUDA, "cudaGetSymbolAddress(g_noalloc_scratch) failed");
-            g_dev_ptr[dev] = p;
-        }
-        base = static_cast<unsigned char *>(g_dev_ptr[dev]);
+        cudaError_t e = cudaGetSymbolAddress(&sym, g_noalloc_scratch);
+        if (e != cudaSuccess || !sym) return nfail(GPE_ECUDA, "cudaGetSymbolAddress(g_noalloc_scratch) failed");
     }
+    unsigned char *base = static_cast<unsigned char *>(sym);
     cudaStream_t st = (cudaStream_t)cuda_stream;
 
     // Tables and parameters of this call.  The array keeps the previous call's
