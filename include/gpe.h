@@ -167,6 +167,15 @@ gpe_status gpe_spectrum(gpe_plan *plan, const void *psi_dev, unsigned kinds, dou
  *                        The one exception to bit-identical results: with
  *                        this option imaginary-time steps can differ in the
  *                        last place (real-time steps do not).
+ *   GPE_OPT_NO_DITHER    1: turns off the phase dither of complex64
+ *                        real-time steps (the default, 0, keeps it): each
+ *                        step's kinetic substep also turns the state by a
+ *                        global phase of at most 0.01 rad and the nonlinear
+ *                        substep of the same step turns it back, which changes
+ *                        the results by rounding only and keeps the rounding
+ *                        errors of slowly turning modes from adding up
+ *                        coherently (norm drift).  Unlike the options above
+ *                        it changes the bits of complex64 results.
  *   GPE_OPT_TEST_STALL_COPIES  test hook for the failure handling: 1 makes
  *                        every copy-engine tile wait expect 16 bytes more than
  *                        its copies deliver, so the wait runs out after its
@@ -183,6 +192,7 @@ enum gpe_option {
     GPE_OPT_TMA_Y = 5,
     GPE_OPT_TMA_Z = 6,
     GPE_OPT_GENERIC_PASSES = 7,
+    GPE_OPT_NO_DITHER = 8,
     GPE_OPT_TEST_STALL_COPIES = 99
 };
 gpe_status gpe_plan_set_option(gpe_plan *plan, int option, int64_t value);
@@ -226,13 +236,30 @@ gpe_status gpe_trace_read(gpe_plan *plan, int i, char *name, size_t name_len, in
  * Limit: N / n[a] <= GPE_NOALLOC_MAX_LINES on every axis (for example 1024^2,
  * 4096 x 32, 128^3); larger grids, and descriptions with V_host, are rejected
  * with GPE_EUNSUPPORTED.
- * The first call made on a device looks up the array's device address there
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call looks up the array's address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing once the library's device
+ * code is loaded).  With lazy module loading (the CUDA default) the first call
+ * on a device loads this library's device code there, which is when the array
+ * and the code take their device memory, outside any framework's allocator:
+ * a framework-managed caller should make one call during its set-up.
+ * The call ends with a device-to-host copy into out_host and synchronises
+ * cuda_stream, so it must not be called while that stream is being captured.
  * Every call reuses the same array, so calls that overlap on the GPU (from
- * other streams or threads) race: serialise them.  Synchronises cuda_stream. */
+ * other streams or threads) race: serialise them.
+ * The twiddles of its transforms are evaluated on the device, those of a plan
+ * on the host, so the results can differ from gpe_norm_energy's in the last
+ * place. */
 #define GPE_NOALLOC_MAX_LINES 32768
 gpe_status gpe_norm_energy_noalloc(const gpe_plan_desc *desc, const void *psi_dev, void *cuda_stream,
                                    double *out_host);
+
+/* Measured double-precision FMA throughput of the current device (a
+ * measurement aid for the roofline of complex128 runs, which are bound by
+ * FP64 arithmetic rather than HBM; no counterpart in the paper).  Launches a
+ * kernel of independent FMA chains on every SM on cuda_stream, synchronises
+ * it, and writes the best of three timed launches to *flops_per_s (2 flops
+ * per FMA).  GPE_EINVAL for a NULL pointer, GPE_ECUDA on a launch error. */
+gpe_status gpe_measure_fp64_peak(void *cuda_stream, double *flops_per_s);
 
 /* Thread-local message describing the last error (never NULL). */
 const char *gpe_last_error(void);

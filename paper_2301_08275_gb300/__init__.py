@@ -32,7 +32,7 @@ EXPORTS = ["gpe_plan_create", "gpe_plan_destroy", "gpe_step_real", "gpe_step_rea
            "gpe_batch_create", "gpe_batch_destroy", "gpe_batch_step_real", "gpe_batch_norm_energy",
            "gpe_batch_groups", "gpe_server_create", "gpe_server_destroy", "gpe_serve_submit", "gpe_serve_poll",
            "gpe_server_stats", "gpe_plan_set_option", "gpe_plan_get_option",
-           "gpe_plan_autotune"]
+           "gpe_plan_autotune", "gpe_measure_fp64_peak"]
 
 
 class GpeError(RuntimeError):
@@ -127,6 +127,7 @@ def lib():
         L.gpe_plan_get_option.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
         L.gpe_plan_autotune.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
         L.gpe_trace_count.argtypes = [vp]
+        L.gpe_measure_fp64_peak.argtypes = [vp, dp]
         L.gpe_trace_read.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t,
                                      ctypes.POINTER(i64), dp]
         for name in EXPORTS:
@@ -211,6 +212,7 @@ def gpe_norm_energy_noalloc(desc, psi_ptr, stream=None):
 
 GPE_OPT_TMA_STAGING, GPE_OPT_TILE_X, GPE_OPT_TILE_Y, GPE_OPT_TILE_Z, GPE_OPT_TMA_Y, GPE_OPT_TMA_Z = 1, 2, 3, 4, 5, 6
 GPE_OPT_GENERIC_PASSES = 7
+GPE_OPT_NO_DITHER = 8
 GPE_OPT_TEST_STALL_COPIES = 99
 GPE_TUNE_NO_TMA = 1
 
@@ -228,6 +230,13 @@ def gpe_plan_get_option(plan, option):
 def gpe_plan_autotune(plan, psi_ptr, reps=3, flags=0):
     """psi_ptr: device address of a state to time on (read only), or 0 for zeros."""
     _check(lib().gpe_plan_autotune(plan, ctypes.c_void_p(psi_ptr or None), int(reps), int(flags)))
+
+
+def gpe_measure_fp64_peak(stream=0):
+    """Measured FP64 FMA throughput of the current device in FLOP/s."""
+    out = ctypes.c_double(0.0)
+    _check(lib().gpe_measure_fp64_peak(ctypes.c_void_p(stream or None), ctypes.byref(out)))
+    return out.value
 
 
 def gpe_trace_enable(plan, enable=True):

@@ -32,6 +32,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace gpe {
 
@@ -45,6 +46,19 @@ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(
 
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+// complex64: both components in one packed two-lane instruction (same
+// round-to-nearest result per component, half the issue slots)
+template <> __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub(float2 a, float2 b)
+{
+    unsigned long long ra, rb, rd;
+    memcpy(&ra, &a, 8);
+    memcpy(&rb, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    memcpy(&d, &rd, 8);
+    return d;
+}
 template <typename C> __device__ __forceinline__ C cmul(C a, C b)
 {
     return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -116,44 +130,101 @@ template <int DIR, typename C> __device__ __forceinline__ C mul_i(C a)
     return mk(-a.y, a.x);
 }
 
-// a * exp(DIR * 2 pi i * K / M) for M <= 16 with K a compile-time constant
-// after unrolling; cos/sin of multiples of pi/8 written out.
+// cos and sin of 2 pi j / 32 for j = 1, 2, 3 (the other non-trivial angles
+// of a 32-point transform follow by symmetry), and their single-precision
+// hi + lo splits: hi = fl(v), lo = fl(v - hi)
+struct Trig32 {
+    static constexpr double c[4] = {1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708};
+    static constexpr double s[4] = {0.0, 0.19509032201612826785, 0.38268343236508977173, 0.55557023301960222474};
+};
+// a * (c + i s) for constants c, s close to a unit factor; in single
+// precision with hi + lo constants so that only the result is rounded
+template <int J> __device__ __forceinline__ float2 cconst_mul(float2 a, bool swap_cs, float sc, float ss)
+{
+    constexpr float ch = (float)Trig32::c[J], cl = (float)(Trig32::c[J] - (double)(float)Trig32::c[J]);
+    constexpr float sh = (float)Trig32::s[J], sl = (float)(Trig32::s[J] - (double)(float)Trig32::s[J]);
+    // (c, s) or (s, c), each with a sign
+    const float c_h = (swap_cs ? sh : ch) * sc, c_l = (swap_cs ? sl : cl) * sc;
+    const float s_h = (swap_cs ? ch : sh) * ss, s_l = (swap_cs ? cl : sl) * ss;
+    const float tx = fmaf(a.x, c_l, -a.y * s_l);
+    const float ty = fmaf(a.x, s_l, a.y * c_l);
+    return mk(fmaf(a.x, c_h, fmaf(-a.y, s_h, tx)), fmaf(a.x, s_h, fmaf(a.y, c_h, ty)));
+}
+template <int J> __device__ __forceinline__ double2 cconst_mul(double2 a, bool swap_cs, double sc, double ss)
+{
+    constexpr double cj = Trig32::c[J], sj = Trig32::s[J];
+    const double c = (swap_cs ? sj : cj) * sc;
+    const double s = (swap_cs ? cj : sj) * ss;
+    return mk(fma(a.x, c, -a.y * s), fma(a.x, s, a.y * c));
+}
+
+// a * exp(DIR * 2 pi i * K / M) for M <= 32 with K a compile-time constant
+// after unrolling.  Multiples of pi/2 are exact; odd multiples of pi/4 carry
+// 1/sqrt(2) to twice the working precision; the other multiples of pi/16 use
+// hi + lo constants (single precision), so none of these factors has a
+// systematic modulus error.
 template <int M, int DIR, typename C> __device__ __forceinline__ C twc(C a, int K)
 {
     using R = decltype(a.x);
-    const int idx = (K * (16 / M)) & 15;
+    const int idx = (K * (32 / M)) & 31;
     if (idx == 0) return a;
-    if (idx == 4) return mul_i<DIR>(a);
-    if (idx == 8) return mk(-a.x, -a.y);
-    if (idx == 12) return mul_i<-DIR>(a);
-    if (idx == 2 || idx == 6 || idx == 10 || idx == 14) {
-        // (+-1 +- i)/sqrt(2): exp(DIR i pi idx/8) = (cx + i sy DIR)/sqrt(2)
-        const R cx = (idx == 2 || idx == 14) ? (R)1 : (R)-1;
-        const R sy = ((idx == 2 || idx == 6) ? (R)1 : (R)-1) * (R)DIR;
+    if (idx == 8) return mul_i<DIR>(a);
+    if (idx == 16) return mk(-a.x, -a.y);
+    if (idx == 24) return mul_i<-DIR>(a);
+    if ((idx & 7) == 4) {
+        // (+-1 +- i)/sqrt(2): exp(DIR i pi idx/16) = (cx + i sy DIR)/sqrt(2)
+        const R cx = (idx == 4 || idx == 28) ? (R)1 : (R)-1;
+        const R sy = ((idx == 4 || idx == 12) ? (R)1 : (R)-1) * (R)DIR;
         return mk(mul_rsqrt2(cx * a.x - sy * a.y), mul_rsqrt2(sy * a.x + cx * a.y));
     }
-    // cos(2 pi idx / 16), sin(2 pi idx / 16)
-    const R c1 = (R)0.92387953251128675613, s1 = (R)0.38268343236508977173, h = (R)0.70710678118654752440;
-    R c, s;
-    switch (idx) {
-    case 1: c = c1; s = s1; break;
-    case 2: c = h; s = h; break;
-    case 3: c = s1; s = c1; break;
-    case 5: c = -s1; s = c1; break;
-    case 6: c = -h; s = h; break;
-    case 7: c = -c1; s = s1; break;
-    case 9: c = -c1; s = -s1; break;
-    case 10: c = -h; s = -h; break;
-    case 11: c = -s1; s = -c1; break;
-    case 13: c = s1; s = -c1; break;
-    case 14: c = h; s = -h; break;
-    default: c = c1; s = -s1; break;   // 15
-    }
-    if (DIR < 0) s = -s;
-    return mk(a.x * c - a.y * s, a.x * s + a.y * c);
+    // angle 2 pi idx / 32 = q pi/2 + j pi/16 with j in 1..3 (first quadrant
+    // reference angle j or 8 - j)
+    const int q = idx >> 3, j = idx & 7;          // j in {1,2,3,5,6,7}
+    const bool sw = j > 4;                         // reference angle (8 - j): swap cos and sin
+    const int jj = sw ? 8 - j : j;
+    // cos and sin of the angle in quadrant q: signs and swap
+    //   q=0: ( c,  s); q=1: (-s,  c); q=2: (-c, -s); q=3: ( s, -c)
+    // with (c, s) = (cos, sin)(jj pi/16) or swapped when sw
+    const bool qs = (q & 1) != 0;
+    const bool swap_cs = sw != qs;
+    const R sgn_c = (q == 1 || q == 2) ? (R)-1 : (R)1;
+    const R sgn_s = ((q >= 2) ? (R)-1 : (R)1) * (R)DIR;
+    if (jj == 1) return cconst_mul<1>(a, swap_cs, sgn_c, sgn_s);
+    if (jj == 2) return cconst_mul<2>(a, swap_cs, sgn_c, sgn_s);
+    return cconst_mul<3>(a, swap_cs, sgn_c, sgn_s);
 }
 
-// In-register DFT of size M (1, 2, 4, 8, 16): even/odd split (radix-2 DIT),
+// one radix-2 step of the M-point DFT: lo = e + W^k o, hi = e - W^k o with
+// W = exp(DIR 2 pi i / M).  The factors 1, -1 and +-i are folded into the
+// additions (no negated or swapped operand is formed); the others multiply
+// first and add with packed instructions.
+template <int M, int DIR, typename C> __device__ __forceinline__ void bfly(C e, C o, int k, C &lo, C &hi)
+{
+    const int idx = (k * (32 / M)) & 31;
+    if (idx == 0) {
+        lo = cadd(e, o);
+        hi = csub(e, o);
+    } else if (idx == 16) {
+        lo = csub(e, o);
+        hi = cadd(e, o);
+    } else if (idx == 8 || idx == 24) {
+        // W^k = s i, s = +-1: e + s i o = (e.x - s o.y, e.y + s o.x)
+        const bool plus = (idx == 8) == (DIR > 0);
+        if (plus) {
+            lo = mk(e.x - o.y, e.y + o.x);
+            hi = mk(e.x + o.y, e.y - o.x);
+        } else {
+            lo = mk(e.x + o.y, e.y - o.x);
+            hi = mk(e.x - o.y, e.y + o.x);
+        }
+    } else {
+        const C t = twc<M, DIR>(o, k);
+        lo = cadd(e, t);
+        hi = csub(e, t);
+    }
+}
+
+// In-register DFT of size M (1, 2, 4, 8, 16, 32): even/odd split (radix-2 DIT),
 // natural-order input and output.  DIR = -1 forward, +1 inverse.
 template <int M, int DIR, typename C> struct Dft {
     __device__ __forceinline__ static void run(C *x)
@@ -164,11 +235,7 @@ template <int M, int DIR, typename C> struct Dft {
         Dft<M / 2, DIR, C>::run(e);
         Dft<M / 2, DIR, C>::run(o);
 #pragma unroll
-        for (int k = 0; k < M / 2; ++k) {
-            C t = twc<M, DIR>(o[k], k);
-            x[k] = cadd(e[k], t);
-            x[k + M / 2] = csub(e[k], t);
-        }
+        for (int k = 0; k < M / 2; ++k) bfly<M, DIR>(e[k], o[k], k, x[k], x[k + M / 2]);
     }
 };
 template <int DIR, typename C> struct Dft<1, DIR, C> {
@@ -194,6 +261,26 @@ template <int N> struct Radix {
     __host__ __device__ static constexpr int radix(int p) { return N < 8 ? N : ((REM && p == 0) ? (1 << REM) : 8); }
     __host__ __device__ static constexpr int ns(int p) { return p == 0 ? 1 : ns(p - 1) * radix(p - 1); }
 };
+// Pass plan for threads holding 32 points of a line (N >= 32): a radix-32
+// first pass (no twiddles), then the remaining log2(N/32) bits in passes of
+// at most 32: 256 = 32 x 8, 512 = 32 x 16, 1024 = 32 x 32, 2048 = 32 x 8 x 8,
+// 4096 = 32 x 16 x 8.  Each transform then needs one shared-memory exchange
+// per pass after the first (one for 256..1024 points, against two with
+// radix-8 passes).
+template <int N> struct Radix32 {
+    static constexpr int LG = ilog2c(N);
+    static constexpr int E = 32;
+    static constexpr int REST = LG - 5;
+    static constexpr int P = REST <= 0 ? 1 : (REST <= 5 ? 2 : 3);
+    __host__ __device__ static constexpr int radix(int p)
+    {
+        return p == 0 ? (N < 32 ? N : 32)
+                      : (P == 2 ? (1 << REST) : (p == 1 ? (1 << (REST - REST / 2)) : (1 << (REST / 2))));
+    }
+    __host__ __device__ static constexpr int ns(int p) { return p == 0 ? 1 : ns(p - 1) * radix(p - 1); }
+};
+template <int N, int E> struct PassPlan { using T = Radix<N>; };
+template <int N> struct PassPlan<N, 32> { using T = Radix32<N>; };
 
 // ---------------------------------------------------------------- tile engine
 // ROWS = true : lines are contiguous rows (x axis); shared layout row-major with
@@ -286,12 +373,15 @@ template <typename R, int N, int L, bool ROWS> struct Tile {
 //
 // EPT points per thread (0: Radix<N>::E = 8): with 16, each pass runs two
 // butterflies per thread (more independent work per thread, half the threads
-// per line); the arithmetic of every butterfly is the same.
+// per line); the arithmetic of every butterfly is the same.  With 32 the
+// passes follow Radix32 (a radix-32 first pass, one exchange fewer per
+// transform for 256 to 1024 points).
 template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struct GTile {
     using C = typename CT<R>::C;
     using U = typename UT<R>::U;
     static constexpr int E = EPT ? EPT : Radix<N>::E;
-    static_assert(E >= Radix<N>::E && N % E == 0, "points per thread must cover the largest radix");
+    using PL = typename PassPlan<N, E>::T;      // radix of each pass
+    static_assert(E >= PL::radix(0) && N % E == 0, "points per thread must cover the largest radix");
     static constexpr int TPL = N / E;
     static constexpr int NP = L / LPT;
     static constexpr int NT = NP * TPL;
@@ -299,7 +389,7 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
     static_assert(L % LPT == 0, "lines per tile must be a multiple of lines per thread");
 
     static constexpr int QS = 128 / (L * (int)sizeof(C)) > 1 ? 128 / (L * (int)sizeof(C)) : 1;
-    static constexpr int SWS = ilog2c(Radix<N>::radix(0));
+    static constexpr int SWS = ilog2c(PL::radix(0));
     __host__ __device__ __forceinline__ static int sidx(int i, int l)
     {
         if constexpr (SW) return (i ^ ((i >> SWS) & (QS - 1))) * L + l;
@@ -332,6 +422,13 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
             for (int ln = 0; ln < LPT; ++ln) v[ln][e] = sm[i0 + ln];
         }
     }
+    // the same without the swizzle (point i of line l at i*L + l)
+    __device__ __forceinline__ static void ld_plain(const C *sm, int tl, int e, int l0, C (&v)[LPT][E])
+    {
+        const int i0 = (tl + TPL * e) * L + l0;
+#pragma unroll
+        for (int ln = 0; ln < LPT; ++ln) v[ln][e] = sm[i0 + ln];
+    }
     // swizzled point index before the line interleave
     __host__ __device__ static constexpr int sraw(int i) { return SW ? (i ^ ((i >> SWS) & (QS - 1))) : i; }
     // Index of Stockham output base + m*Ns of a pass.  base and m*Ns occupy
@@ -359,9 +456,9 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
     // conflicts) and each thread's r-1 reads sit at constant offsets.
     __host__ __device__ static constexpr int tw_off(int p)
     {
-        return p <= 1 ? 0 : tw_off(p - 1) + Radix<N>::ns(p - 1) * (Radix<N>::radix(p - 1) - 1);
+        return p <= 1 ? 0 : tw_off(p - 1) + PL::ns(p - 1) * (PL::radix(p - 1) - 1);
     }
-    static constexpr int TWN = tw_off(Radix<N>::P);
+    static constexpr int TWN = tw_off(PL::P);
     // fill the pass-ordered table from the natural one (W_N^t, t < N)
     __device__ __forceinline__ static void load_twiddles(U *tws, const U *__restrict__ twg, int t, int nt)
     {
@@ -369,10 +466,10 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
     }
     template <int p> __device__ __forceinline__ static int tw_src(int idx)
     {
-        if constexpr (p >= Radix<N>::P) {
+        if constexpr (p >= PL::P) {
             return 0;
         } else {
-            constexpr int ns = Radix<N>::ns(p), r = Radix<N>::radix(p);
+            constexpr int ns = PL::ns(p), r = PL::radix(p);
             const int rel = idx - tw_off(p);
             if (rel < ns * (r - 1)) {
                 const int m = rel / ns + 1, k = rel % ns;
@@ -396,10 +493,10 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
     __device__ __forceinline__ static void pass(C (&v)[LPT][E], C *sb, C *ss, int tl, int l0,
                                                 const U *__restrict__ tw)
     {
-        constexpr int r = Radix<N>::radix(p);
-        constexpr int Ns = Radix<N>::ns(p);
+        constexpr int r = PL::radix(p);
+        constexpr int Ns = PL::ns(p);
         constexpr int B = E / r;
-        constexpr bool last = (p == Radix<N>::P - 1);
+        constexpr bool last = (p == PL::P - 1);
         C *const rd = (PING && p % 2 == 1) ? ss : sb;    // written by pass p-1
         C *const wr = (PING && p % 2 == 0) ? ss : sb;
         if constexpr (p > 0) {
@@ -407,7 +504,7 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
 #pragma unroll
             for (int e = 0; e < E; ++e) ld(rd, tl, e, l0, v);
             if constexpr (!last && !PING) __syncthreads();
-        } else if constexpr (!last && (!PING || Radix<N>::P % 2 == 0)) {
+        } else if constexpr (!last && (!PING || PL::P % 2 == 0)) {
             __syncthreads();
         }
 #pragma unroll
@@ -452,7 +549,7 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
     template <int DIR, bool PING = false, int p = 0>
     __device__ __forceinline__ static void fft(C (&v)[LPT][E], C *sb, C *ss, int tl, int l0, const U *tw)
     {
-        if constexpr (p < Radix<N>::P) {
+        if constexpr (p < PL::P) {
             pass<DIR, p, PING>(v, sb, ss, tl, l0, tw);
             fft<DIR, PING, p + 1>(v, sb, ss, tl, l0, tw);
         }

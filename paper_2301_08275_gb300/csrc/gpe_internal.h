@@ -58,6 +58,13 @@ struct PassArgs {
     const void *vsamp, *vsamp_diag;
     const double *g;       // per-instance interaction
     double nl_c;           // theta = g * nl_c * |psi|^2
+    // per-step phase dither of the complex64 real-time step: the kinetic
+    // substep multiplies by exp(-i phi) as well (dk: its offset exp(-i phi) - 1
+    // as a hi, hi, lo, lo float quadruple stored in doubles) and the following
+    // nonlinear substep by exp(+i phi) (dphi = phi); 0 when off
+    int dither;
+    double dk[4];
+    double dphi;
     double inv_n;          // 1/N applied with the kinetic substep
     const double *scale;   // per-instance renormalisation factor
     // optional indirection for batches of separately allocated instances:

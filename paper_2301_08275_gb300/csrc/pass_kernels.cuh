@@ -163,6 +163,50 @@ __device__ __forceinline__ double line_sum(double x, double *red, int l, int tl)
     return r;
 }
 
+// Offset of a product of two unit factors held as offsets a, b from one:
+// (1 + a)(1 + b) - 1 = a + b + ab, summed with error-free transformations
+// (two-sum, two-product) and returned as a hi + lo float pair, so that the
+// product is applied in offset form (v + v c, see uomul) with one rounding.
+// The unit-factor form (umul) of the same product would be biased for small
+// angles: its real part rounds to exactly one, and the inner fused product
+// v.y * 1 + (tiny) then rounds the second-order term away every time (a
+// norm gain of about angle^2 / 2 per application).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ float4 offset_product(float4 a, float4 b)
+{
+    // ab: exact products of the hi parts, the cross terms with the lo parts
+    // in plain arithmetic (of order 1e-8 |ab|)
+    const float p1 = a.x * b.x, e1 = fmaf(a.x, b.x, -p1);
+    const float p2 = a.y * b.y, e2 = fmaf(a.y, b.y, -p2);
+    const float p3 = a.x * b.y, e3 = fmaf(a.x, b.y, -p3);
+    const float p4 = a.y * b.x, e4 = fmaf(a.y, b.x, -p4);
+    const float xl = (e1 - e2) + ((a.x * b.z + a.z * b.x) - (a.y * b.w + a.w * b.y));
+    const float yl = (e3 + e4) + ((a.x * b.w + a.z * b.y) + (a.y * b.z + a.w * b.x));
+    float sx, ex, t, tx, ux, vx;
+    two_sum(p1, -p2, sx, ex);
+    two_sum(a.x, b.x, t, tx);
+    two_sum(t, sx, ux, vx);
+    const float lx = vx + (tx + (ex + (xl + (a.z + b.z))));
+    float sy, ey, ty, uy, vy;
+    two_sum(p3, p4, sy, ey);
+    two_sum(a.y, b.y, t, ty);
+    two_sum(t, sy, uy, vy);
+    const float ly = vy + (ty + (ey + (yl + (a.w + b.w))));
+    float hx, gx, hy, gy;
+    two_sum(ux, lx, hx, gx);
+    two_sum(uy, ly, hy, gy);
+    return make_float4(hx, hy, gx, gy);
+}
+__device__ __forceinline__ double2 offset_product(double2 a, double2 b)
+{
+    return make_double2(a.x + b.x + (a.x * b.x - a.y * b.y), a.y + b.y + (a.x * b.y + a.y * b.x));
+}
+
 // pointwise substep on the E points (indices tl + TPL*e on this axis) of one line
 // inst: position of the instance in this launch (renormalisation factor);
 // ti: its parameter/table slot
@@ -180,14 +224,20 @@ __device__ __forceinline__ void point_op(int op, typename CT<R>::C (&v)[E], cons
         const R invn = (R)a.inv_n;
         const U *k0 = static_cast<const U *>(a.kt_o0);
         const U *k1 = static_cast<const U *>(a.kt_o1);
-        const U f0 = k0 ? k0[c0] : U{}, f1 = k1 ? k1[c1] : U{};
+        if (!k0 && !k1) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            C x = uomul(v[e], kt[tl + TPL * e]);
-            if (k0) x = uomul(x, f0);
-            if (k1) x = uomul(x, f1);
-            v[e] = cscale(x, invn);
+            for (int e = 0; e < E; ++e) v[e] = cscale(uomul(v[e], kt[tl + TPL * e]), invn);
+            return;
         }
+        // the factors of the line's other axes, combined once per line into
+        // one offset to twice the working precision
+        U fl = offset_product(k0 ? k0[c0] : U{}, k1 ? k1[c1] : U{});
+        if constexpr (sizeof(R) == 4) {
+            if (a.dither)
+                fl = offset_product(fl, make_float4((float)a.dk[0], (float)a.dk[1], (float)a.dk[2], (float)a.dk[3]));
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = cscale(uomul(uomul(v[e], kt[tl + TPL * e]), fl), invn);
         return;
     }
     if (op == OP_KIMAG) {
@@ -216,15 +266,17 @@ __device__ __forceinline__ void point_op(int op, typename CT<R>::C (&v)[E], cons
         // separate paths with and without a sampled potential keep the
         // common one free of its address arithmetic (fewer live registers)
         R th[E];
+        const R dphi = (R)a.dphi;      // undoes the kinetic substep's dither (0 when off)
         if (a.vsamp) {
             const R *vs = static_cast<const R *>(a.vsamp) + off;
             const R cc = (R)a.nl_c;
 #pragma unroll
-            for (int e = 0; e < E; ++e) th[e] = fma(vs[(int64_t)(tl + TPL * e) * a.estride], cc, gc * cabs2(v[e]));
+            for (int e = 0; e < E; ++e)
+                th[e] = fma(vs[(int64_t)(tl + TPL * e) * a.estride], cc, gc * cabs2(v[e])) - dphi;
             apply_phase<C, R, E>(v, th);
         } else {
 #pragma unroll
-            for (int e = 0; e < E; ++e) th[e] = gc * cabs2(v[e]);
+            for (int e = 0; e < E; ++e) th[e] = gc * cabs2(v[e]) - dphi;
             apply_phase<C, R, E>(v, th);
         }
 #pragma unroll
@@ -393,11 +445,25 @@ template <typename R> __host__ __device__ constexpr int lines_per_thread() { ret
 // same order whichever shape the tuner picks.
 template <typename R, int N, bool ROWS> __host__ __device__ constexpr int pass_points_per_thread()
 {
-    return (!ROWS && sizeof(R) == 4 && N >= 16) ? 16 : Radix<N>::E;
+    return (!ROWS && sizeof(R) == 4 && N >= 256 && N <= 1024) ? 32
+           : (!ROWS && sizeof(R) == 4 && N >= 16)              ? 16
+                                                               : Radix<N>::E;
 }
 
+// Shared layout of the transform exchanges.  Rows of the split tiles are
+// swizzled (see rows_split).  Strided tiles with 32 points per thread and
+// fewer than 16 lines swizzle too: the first pass writes points 32 apart from
+// lanes whose tl differ, which fall into the same banks when a point row
+// (L lines) is narrower than 128 bytes; the swizzle spreads them over the
+// row.  A tile staged by the copy engine arrives unswizzled and is read with
+// the plain index.
+template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr bool pass_swizzle()
+{
+    return rows_split<R, N, ROWS, VAR>() ||
+           (!ROWS && pass_points_per_thread<R, N, ROWS>() == 32 && pick_lines<R, N, ROWS, VAR>() * (int)sizeof(R) * 2 < 128);
+}
 template <typename R, int N, bool ROWS, int VAR>
-using PassTile = GTile<R, N, pick_lines<R, N, ROWS, VAR>(), lines_per_thread<R>(), rows_split<R, N, ROWS, VAR>(),
+using PassTile = GTile<R, N, pick_lines<R, N, ROWS, VAR>(), lines_per_thread<R>(), pass_swizzle<R, N, ROWS, VAR>(),
                        pass_points_per_thread<R, N, ROWS>()>;
 
 // dynamic shared memory of one CTA without the transform scratch: two staging
@@ -415,7 +481,11 @@ template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr i
 {
     constexpr int nt = PassTile<R, N, ROWS, VAR>::NT;
     constexpr int want = 1024 / nt > 16 ? 16 : 1024 / nt;
-    constexpr int b = rows_split<R, N, ROWS, VAR>() && want > 2 ? want : (nt > 512 ? 1 : 2);
+    // strided tiles of 32 points per thread: as many CTAs as the shared memory
+    // holds (registers are then capped accordingly: 3 CTAs of 128 threads,
+    // 170 registers)
+    constexpr bool wide = !ROWS && pass_points_per_thread<R, N, ROWS>() == 32;
+    constexpr int b = (rows_split<R, N, ROWS, VAR>() || wide) && want > 2 ? want : (nt > 512 ? 1 : 2);
     constexpr int fit = (int)(227 * 1024 / (pass_smem_base<R, N, ROWS, VAR>() + 1024));
     return b < fit ? b : (fit > 0 ? fit : 1);
 }
@@ -428,7 +498,7 @@ template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr b
 {
     using T = PassTile<R, N, ROWS, VAR>;
     constexpr size_t with = pass_smem_base<R, N, ROWS, VAR>() + sizeof(typename T::C) * T::SMEM_POINTS;
-    return Radix<N>::P > 1 && pass_min_blocks<R, N, ROWS, VAR>() == 1 && with + 1024 <= 227 * 1024;
+    return T::PL::P > 1 && pass_min_blocks<R, N, ROWS, VAR>() == 1 && with + 1024 <= 227 * 1024;
 }
 template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr size_t pass_smem_bytes()
 {
@@ -571,7 +641,10 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
         for (int ln = 0; ln < LPT; ++ln) g[ln] = line_geom<L>(a, tile, l0 + ln);
         C v[LPT][E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) T::ld(sm, tl, e, l0, v);
+        for (int e = 0; e < E; ++e) {
+            if (tma) T::ld_plain(sm, tl, e, l0, v);    // the copy engine's tile is unswizzled
+            else T::ld(sm, tl, e, l0, v);
+        }
 #pragma unroll
         for (int ln = 0; ln < LPT; ++ln)
             if (!g[ln].valid)
@@ -934,12 +1007,28 @@ template <typename R, int N> static cudaError_t launch_line1d_t(const Line1DArgs
 
 #define GPE_FOR_EACH_N(X) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
 
+// Strided complex64 lines of 256 to 1024 points (radix-32 kernels, the
+// longest to compile) are instantiated in translation units of their own,
+// one per line length and tile shape (pass_f32_w<N>_<VAR>.cu), so that the
+// library builds in parallel.
+template <int N, int VAR> cudaError_t launch_pass_wide_f32(const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap);
+template <typename R, int N, bool ROWS> constexpr bool pass_wide_tu()
+{
+    return sizeof(R) == 4 && !ROWS && N >= 256 && N <= 1024;
+}
+template <typename R, int N, bool ROWS, int VAR>
+static cudaError_t launch_pass_n(const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap)
+{
+    if constexpr (pass_wide_tu<R, N, ROWS>()) return launch_pass_wide_f32<N, VAR>(a, st, tmap);
+    else return launch_pass_t<R, N, ROWS, VAR>(a, st, tmap);
+}
+
 template <typename R, bool ROWS, int VAR>
 static cudaError_t launch_pass_r(const PassArgs &a, cudaStream_t st, const CUtensorMap *tmap)
 {
     switch (a.nax) {
 #define GPE_CASE(NN) \
-    case NN: return launch_pass_t<R, NN, ROWS, VAR>(a, st, tmap);
+    case NN: return launch_pass_n<R, NN, ROWS, VAR>(a, st, tmap);
         GPE_FOR_EACH_N(GPE_CASE)
 #undef GPE_CASE
     default: return cudaErrorInvalidValue;
