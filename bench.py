@@ -31,22 +31,24 @@ sys.path.insert(0, ROOT)
 import gpe_inputs as gi  # noqa: E402
 
 WORKLOADS = {
-    "tg512": dict(spec=gi.CONFIG_3D_TG, prec="c64",
+    "tg512": dict(spec=gi.CONFIG_3D_TG, prec="c64", length=1000,
                   name="3D Taylor-Green 512^3, complex64 bulk / FP64 tables and reductions, real time, "
                        "dt=1e-3, V=0, g=1, box side 2*pi*16"),
-    "turb1024": dict(spec=gi.CONFIG_2D, prec="c64", spectra_every=200,
+    "turb1024": dict(spec=gi.CONFIG_2D, prec="c64", spectra_every=200, length=2000,
                      name="2D quantum turbulence 1024^2, complex64, real time, dt=5e-4, V=0, g=1, "
                           "512 vortices, box side 2*pi*32; incompressible/compressible spectra every 200 steps"),
-    "turb1024c128": dict(spec=gi.CONFIG_2D, prec="c128", spectra_every=200,
+    "turb1024c128": dict(spec=gi.CONFIG_2D, prec="c128", spectra_every=200, length=2000,
                          name="2D quantum turbulence 1024^2, complex128, real time, dt=5e-4, V=0, g=1, "
                               "512 vortices, box side 2*pi*32; incompressible/compressible spectra every 200 steps"),
-    "line256": dict(spec=gi.CONFIG_1D, prec="c128",
+    "line256": dict(spec=gi.CONFIG_1D, prec="c128", length=1000,
                     name="1D 256 points complex128, real time, dt=1e-3, V=x^2/2, g=10"),
 }
 METRIC = "TSSP grid-point updates/s vs HBM roofline"
 UNIT = "grid-point updates/s"
 KERNEL_SOURCES = ["fft_tile.cuh", "pass_kernels.cuh", "pass_f32.cu", "pass_f32_s1.cu", "pass_f32_rows.cu",
-                  "pass_f32_rows1.cu", "pass_f64.cu", "pass_f64_s1.cu", "pass_f64_rows.cu", "pass_f64_rows1.cu"]
+                  "pass_f32_rows1.cu", "pass_f32_w256_0.cu", "pass_f32_w256_1.cu", "pass_f32_w512_0.cu",
+                  "pass_f32_w512_1.cu", "pass_f32_w1024_0.cu", "pass_f32_w1024_1.cu", "pass_f64.cu",
+                  "pass_f64_s1.cu", "pass_f64_rows.cu", "pass_f64_rows1.cu"]
 
 
 def initial_state(key, spec, seed=0):
@@ -162,9 +164,11 @@ def dist_setup():
     return ws, rank, local
 
 
-def cpu_sample(key, spec, max_seconds=25.0, steps=None):
+def cpu_sample(key, spec, max_seconds=25.0, steps=None, max_steps=None):
     """Time the FP64 oracle on the host cores: whole-grid steps of the workload
-    until about max_seconds of work (at least one step)."""
+    until about max_seconds of work (at least one step, at most max_steps).
+    Returns the baseline record, the oracle's state after those steps and
+    their number (the parity check of the GPU run starts from the same input)."""
     import oracle
     oracle.build()
     cores = oracle.set_threads(0)
@@ -175,11 +179,64 @@ def cpu_sample(key, spec, max_seconds=25.0, steps=None):
         psi = P.step_real(psi, 1)
         done += 1
         el = time.perf_counter() - t0
-        if (steps is not None and done >= steps) or (steps is None and (el > max_seconds or el * (done + 1) / done > max_seconds * 1.2)):
+        if (steps is not None and done >= steps) or (max_steps is not None and done >= max_steps) or \
+                (steps is None and (el > max_seconds or el * (done + 1) / done > max_seconds * 1.2)):
             break
-    return dict(value=spec.N * done / el, unit=UNIT, cores=cores, kind="oracle",
-                sample="%d full-grid real-time step(s) of the same workload (%s) on the FP64 oracle, %.1f s"
-                % (done, "x".join(map(str, spec.n)), el))
+    rec = dict(value=spec.N * done / el, unit=UNIT, cores=cores, kind="oracle",
+               sample="%d full-grid real-time step(s) of the same workload (%s) on the FP64 oracle, %.1f s"
+               % (done, "x".join(map(str, spec.n)), el))
+    return rec, psi, done
+
+
+def pass_flops_per_point(kind):
+    """Algorithmic FLOPs per grid point of one sweep, from its trace kind such
+    as 'y1024:F-KR-I': 5 log2(n) per n-point complex transform (the usual
+    radix-2 count) and 6 per pointwise complex multiplication substep."""
+    head, prog = kind.split(":", 1)
+    n = int("".join(ch for ch in head if ch.isdigit()))
+    toks = prog.split("-")
+    ffts = sum(1 for t in toks if t in ("F", "I"))
+    pointwise = sum(1 for t in toks if t not in ("F", "I"))
+    return 5.0 * math.log2(n) * ffts + 6.0 * pointwise
+
+
+def alu_roofline(gpe, stream, kind, avg_ms, npoints, kernels):
+    """Roofline of a complex128 sweep: FP64 arithmetic against the measured
+    FP64 FMA rate of this GPU (complex128 sweeps are bound by it, not HBM)."""
+    peak = gpe.gpe_measure_fp64_peak(stream.cuda_stream) / 1e12
+    flops = pass_flops_per_point(kind) * npoints
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": kind, "kernel_avg_ms": avg_ms, "flops_per_launch": flops,
+            "peak_source": "measured: gpe_measure_fp64_peak (independent FP64 FMA chains on every SM)",
+            "flops_model": "5 log2(n) per n-point transform + 6 per pointwise complex multiply, per point",
+            "kernels": kernels}
+
+
+def gpu_parity(plan, key, spec, prec, ref, nsteps):
+    """The library's state after nsteps from the oracle's input (seed 0), on the
+    plan the bench timed, against the oracle's state: relative L2 error, norm
+    drift over the run and relative energy error, all evaluated by the oracle."""
+    import torch
+    import oracle
+    P = oracle.Problem(**spec.kwargs())
+    psi0 = initial_state(key, spec)
+    dt = np.complex64 if prec == 0 else np.complex128
+    x = torch.from_numpy(np.ascontiguousarray(psi0).astype(dt)).cuda()
+    torch.cuda.synchronize()                 # the upload ran on the default stream
+    plan.step_real(x, nsteps)
+    torch.cuda.synchronize()
+    out = x.cpu().numpy().astype(np.complex128)
+    del x
+    n0 = P.norm_energy(np.asarray(psi0, dtype=dt).astype(np.complex128))
+    e_out, e_ref = P.norm_energy(out), P.norm_energy(ref)
+    diff = float(np.linalg.norm((out - ref).ravel()) / np.linalg.norm(ref.ravel()))
+    return {"steps": int(nsteps), "rel_l2": diff, "norm_drift": float(abs(e_out[0] / n0[0] - 1.0)),
+            "energy_rel": float(abs(e_out[4] - e_ref[4]) / abs(e_ref[4])),
+            "tolerance": ("rel_l2 <= 2e-4, norm_drift <= 1e-6, energy_rel <= 1e-5" if prec == 0
+                          else "rel_l2 <= 1e-12"),
+            "how": "same seeded input on both sides; the library on the timed plan, the FP64 oracle on the host; "
+                   "norm and energy of both states evaluated by the oracle"}
 
 
 def run_reference(args, key, wl):
@@ -334,14 +391,22 @@ def run_ours(args, key, wl):
     kind, (cnt, tot) = dom
     avg_ms = tot / cnt
     bytes_per_launch = 2.0 * spec.N * (8 if prec == gpe.GPE_C64 else 16)
-    peak, peak_src = measured_peaks()
-    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-    traffic = read_traffic(kind, key)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": kind, "kernel_avg_ms": avg_ms,
-                "bytes_per_launch": bytes_per_launch, "peak_source": peak_src,
-                "kernels": {k: {"launches": c, "avg_ms": t / c, "share": t / sum(x[1] for x in tr.values())}
-                            for k, (c, t) in tr.items()}}
+    kernels = {k: {"launches": c, "avg_ms": t / c, "share": t / sum(x[1] for x in tr.values())}
+               for k, (c, t) in tr.items()}
+    state_bytes = spec.N * (8 if prec == gpe.GPE_C64 else 16)
+    if prec == gpe.GPE_C128:
+        roofline = alu_roofline(gpe, stream, kind, avg_ms, spec.N, kernels)
+    else:
+        peak, peak_src = measured_peaks()
+        achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+        traffic = read_traffic(kind, key)
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic, "kernel": kind, "kernel_avg_ms": avg_ms,
+                    "bytes_per_launch": bytes_per_launch, "peak_source": peak_src, "kernels": kernels}
+        if state_bytes < 100e6:
+            roofline["l2_resident"] = ("the %.0f MiB state stays in L2 between launches: HBM bytes do not bind "
+                                       "these launches (each CTA runs one or two tiles; latency bound)"
+                                       % (state_bytes / 2 ** 20))
 
     # end to end through the host-buffer entry point: every step copies the
     # state in from pinned host memory and the result back
@@ -359,9 +424,11 @@ def run_ours(args, key, wl):
            "d2h_bytes_per_step": state_bytes, "steps": e2e_steps,
            "api": "gpe_step_real_host (1 step per call, pinned host buffer)"}
 
-    cpu = None
+    cpu, parity = None, None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_sample(key, spec)
+        cpu, ref_state, ref_steps = cpu_sample(key, spec, max_steps=wl.get("length"))
+        parity = gpu_parity(plan, key, spec, prec, ref_state, ref_steps)
+        del ref_state
 
     cufft = cufft_reference(spec, psi) if (spec.ndim >= 2 and rank == 0) else None
     nrm = plan.norm_energy(psi)[0]
@@ -375,8 +442,8 @@ def run_ours(args, key, wl):
                        if state_bytes > 130e6 else "state fits in L2 (not flushed)",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "tiles": tiles, "norm_after": float(nrm[0])},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "cufft_reference": cufft, "clocks": clk.summary(),
-            "gpu_launches": launches}
+            "roofline": roofline, "cpu_baseline": cpu, "parity": parity, "e2e": e2e, "cufft_reference": cufft,
+            "clocks": clk.summary(), "gpu_launches": launches}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
