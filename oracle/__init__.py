@@ -16,6 +16,10 @@ Parity status of each function (what pins it in ``tests/test_oracle.py``):
   step_real ............ plane wave (exact), norm conservation, time reversal,
                          bright soliton, Bogoliubov frequency, g=0 breathing
                          Gaussian (closed form sigma(t))
+  step_real_trap ....... a constant schedule equals step_real; g=0 quench of
+                         the trap (closed form sigma(t)); g=0 modulated trap
+                         against the moment equations integrated by RK4, with
+                         second-order convergence in dt
   step_imag / ground ... g=0 harmonic ground state (closed form), 2D rows of
                          the paper's Table 1 (soft pin)
   norm_energy .......... closed-form Gaussian energies, plane-wave energy
@@ -77,6 +81,7 @@ def _load():
         lib.orc_fft.argtypes = [cd, ctypes.c_int, P(ctypes.c_long), ctypes.c_int]
         lib.orc_dft_brute.argtypes = [cd, cd, ctypes.c_int, P(ctypes.c_long), ctypes.c_int]
         lib.orc_step_real.argtypes = [cd, G, ctypes.c_long]
+        lib.orc_step_real_trap.argtypes = [cd, G, ctypes.c_long, cd]
         lib.orc_step_imag.argtypes = [cd, G, ctypes.c_long, ctypes.c_double]
         lib.orc_norm_energy.argtypes = [cd, G, P(ctypes.c_double)]
         lib.orc_rms.argtypes = [cd, G, P(ctypes.c_double)]
@@ -183,6 +188,21 @@ class Problem:
         """Advance nsteps real-time TSSP steps; returns a new array."""
         y = _as_c128(psi, self.N).copy()
         _check(_load().orc_step_real(_ptr(y), ctypes.byref(self._g), int(nsteps)), "step_real")
+        return y.reshape(np.shape(psi))
+
+    def step_real_trap(self, psi, gamma_t):
+        """Real-time steps in a trap with time-dependent frequencies: gamma_t is
+        an array of shape (nsteps + 1, ndim), the trap at the time levels of the
+        call; step n uses row n for its first nonlinear half-step and row n + 1
+        for its second.  Returns a new array."""
+        g = np.ascontiguousarray(gamma_t, dtype=np.float64)
+        if g.ndim != 2 or g.shape[1] != len(self.n) or g.shape[0] < 1:
+            raise ValueError("gamma_t must have shape (nsteps + 1, ndim)")
+        g3 = np.zeros((g.shape[0], 3))
+        g3[:, :len(self.n)] = g
+        y = _as_c128(psi, self.N).copy()
+        _check(_load().orc_step_real_trap(_ptr(y), ctypes.byref(self._g), int(g.shape[0] - 1), _ptr(g3)),
+               "step_real_trap")
         return y.reshape(np.shape(psi))
 
     def step_imag(self, psi, nsteps=1, target_norm=1.0):

@@ -316,6 +316,36 @@ int orc_step_real(cplx *psi, const orc_grid *G, long nsteps)
     return 0;
 }
 
+/* Real-time steps in a harmonic trap whose frequencies change in time
+ * (Eq. ndGPE with V(r, t); the paper lists time-dependent potentials among
+ * the solver's functionalities).  gamma_t holds (nsteps + 1) rows of three
+ * trap frequencies, the trap at the time levels t_0 .. t_nsteps of the call.
+ * Step n runs the Strang splitting of step_real_once with the first nonlinear
+ * half-step in the trap of t_n and the second in the trap of t_{n+1}, so each
+ * nonlinear half-step evaluates V at the end of the time interval it is
+ * adjacent to, and the scheme stays symmetric in time.  The sampled
+ * potential G->V, if any, is not used (the schedule is the potential). */
+int orc_step_real_trap(cplx *psi, const orc_grid *G, long nsteps, const double *gamma_t)
+{
+    int e = check_grid(G);
+    if (e) return e;
+    if (!gamma_t) return -1;
+    orc_grid H = *G;
+    H.V = NULL;
+    long N = total_points(G);
+    for (long s = 0; s < nsteps; s++) {
+        for (int a = 0; a < 3; a++) H.gamma[a] = a < G->ndim ? gamma_t[3 * s + a] : 0.0;
+        nonlinear_real(psi, &H, 0.5 * G->dt);
+        orc_fft(psi, G->ndim, G->n, -1);
+        kinetic_real(psi, &H, G->dt);
+        orc_fft(psi, G->ndim, G->n, +1);
+        scale_all(psi, N, 1.0 / (double)N);
+        for (int a = 0; a < 3; a++) H.gamma[a] = a < G->ndim ? gamma_t[3 * (s + 1) + a] : 0.0;
+        nonlinear_real(psi, &H, 0.5 * G->dt);
+    }
+    return 0;
+}
+
 /* One imaginary-time step followed by renormalisation to N0. */
 static int step_imag_once(cplx *psi, const orc_grid *G, double N0)
 {

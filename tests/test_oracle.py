@@ -156,6 +156,75 @@ def test_breathing_gaussian_rms_g0(orc, dt, tol):
     assert abs(r[3] - math.sqrt(sum(v * v for v in r[:3]))) < 1e-14
 
 
+# ---------------------------------------------------------- time-dependent trap
+def test_constant_trap_schedule_is_the_static_trap(orc):
+    """A schedule that keeps the trap fixed runs exactly the static step."""
+    sp = gi.Spec(n=(32, 16), lo=(-6, -4), length=(12, 8), g=20.0, dt=1e-3, gamma=(1.0, 1.7))
+    psi = gi.random_field(sp, seed=2, smooth=0.1)
+    P = orc.Problem(**sp.kwargs())
+    gt = np.tile(np.array([1.0, 1.7]), (8, 1))
+    assert np.array_equal(P.step_real_trap(psi, gt), P.step_real(psi, 7))
+
+
+@pytest.mark.parametrize("dt,tol", [(2e-3, 2e-5), (1e-3, 5e-6)])
+def test_trap_quench_g0_closed_form(orc, dt, tol):
+    """g = 0, the oscillator ground state of gamma0 in a trap switched to
+    gamma1 at t = 0: <x^2>(t) = 1/(2 gamma0) cos^2(gamma1 t)
+    + gamma0/(2 gamma1^2) sin^2(gamma1 t) per axis (Heisenberg evolution of
+    x and p); the schedule holds gamma1 at every time level."""
+    g0, g1 = (1.0, 2.0), (2.0, 1.5)
+    sp = gi.Spec(n=(64, 64), lo=(-8, -8), length=(16, 16), g=0.0, dt=dt, gamma=g0)
+    P = orc.Problem(**sp.kwargs())
+    psi = gi.harmonic_gaussian(sp)
+    T = 0.6
+    ns = int(round(T / dt))
+    psi = P.step_real_trap(psi, np.tile(np.array(g1), (ns + 1, 1)))
+    r = P.rms(psi)
+    for a in range(2):
+        ex = math.sqrt(math.cos(g1[a] * T) ** 2 / (2 * g0[a]) + g0[a] / (2 * g1[a] ** 2) * math.sin(g1[a] * T) ** 2)
+        assert abs(r[a] - ex) / ex < tol
+
+
+def _moments_rk4(w2, x2, xp, p2, T, nsub):
+    """<x^2>, <xp+px>, <p^2> of H = p^2/2 + w(t)^2 x^2/2 (exact moment
+    equations, Heisenberg picture), integrated by classical RK4."""
+    h = T / nsub
+
+    def f(t, y):
+        a, b, c = y
+        return np.array([b, 2 * c - 2 * w2(t) * a, -w2(t) * b])
+
+    y, t = np.array([x2, xp, p2]), 0.0
+    for _ in range(nsub):
+        k1 = f(t, y)
+        k2 = f(t + h / 2, y + h / 2 * k1)
+        k3 = f(t + h / 2, y + h / 2 * k2)
+        k4 = f(t + h, y + h * k3)
+        y = y + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        t += h
+    return y[0]
+
+
+def test_modulated_trap_g0_matches_moment_equations_at_second_order(orc):
+    """g = 0 in a trap whose frequency is modulated, gamma(t) = 1 + 0.5 sin(3 t):
+    the width follows the exact moment equations (integrated to 1e-12 by RK4).
+    The TSSP error must shrink four-fold when dt halves: evaluating V at the
+    wrong time levels would leave a first-order error."""
+    w = lambda t: 1.0 + 0.5 * math.sin(3.0 * t)
+    T = 0.8
+    ref = _moments_rk4(lambda t: w(t) ** 2, 0.5, 0.0, 0.5, T, 20000)
+    errs = []
+    for dt in (4e-3, 2e-3, 1e-3):
+        sp = gi.Spec(n=(256,), lo=(-12,), length=(24,), g=0.0, dt=dt, gamma=(1.0,))
+        P = orc.Problem(**sp.kwargs())
+        ns = int(round(T / dt))
+        gt = np.array([[w(k * dt)] for k in range(ns + 1)])
+        psi = P.step_real_trap(gi.harmonic_gaussian(sp), gt)
+        errs.append(abs(P.rms(psi)[0] ** 2 - ref))
+    assert errs[2] < 2e-6
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
+
+
 # ---------------------------------------------------------- imaginary time
 @pytest.mark.parametrize("spec", [
     gi.Spec(n=(128,), lo=(-10,), length=(20,), g=0.0, dt=1e-3, gamma=(1.0,)),
