@@ -97,6 +97,22 @@ gpe_status gpe_plan_destroy(gpe_plan *plan);
  * on return.  nsteps >= 0. */
 gpe_status gpe_step_real(gpe_plan *plan, void *psi_dev, int64_t nsteps);
 
+/* gpe_step_real in a harmonic trap whose frequencies change in time, V(r, t) =
+ * sum_a gamma_a(t)^2 x_a^2 / 2 (Eq. ndGPE allows any V; the paper lists
+ * time-dependent potentials among the solver's functionalities).  gamma_host
+ * holds (nsteps + 1) rows of three frequencies (x, y, z; axes beyond ndim are
+ * ignored): row n is the trap at time level n of this call, t_n = n dt.  Step
+ * n applies its first nonlinear half-step in the trap of row n and its second
+ * in the trap of row n + 1 (merged with the next step's first half, exact as in
+ * gpe_step_real); the kinetic substep is unchanged.  The schedule replaces the
+ * plan's own trap for this call, on every axis and every instance, and any
+ * axis may be trapped.  A step change of gamma between two rows is a quench at
+ * that time level.  The tables of each time level are built on the device
+ * (host memory is read only during the call).  Diagnostics afterwards still use
+ * the plan's own trap.  GPE_EUNSUPPORTED for plans with V_host; GPE_EINVAL for
+ * NULL or non-finite frequencies or nsteps < 0. */
+gpe_status gpe_step_real_trap(gpe_plan *plan, void *psi_dev, int64_t nsteps, const double *gamma_host);
+
 /* Same as gpe_step_real on a HOST buffer: copies psi in (pageable or pinned),
  * steps on the device and copies the result back.  Uses plan workspace. */
 gpe_status gpe_step_real_host(gpe_plan *plan, void *psi_host, int64_t nsteps);

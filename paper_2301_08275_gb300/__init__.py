@@ -26,7 +26,8 @@ GPE_SPEC_INC, GPE_SPEC_COMP, GPE_SPEC_QP, GPE_SPEC_NUM = 1, 2, 4, 8
 STATUS = {0: "GPE_OK", 1: "GPE_EINVAL", 2: "GPE_EUNSUPPORTED", 3: "GPE_ENOMEM", 4: "GPE_ECUDA",
           5: "GPE_ENUMERIC", 6: "GPE_ETIMEOUT", 7: "GPE_EBUSY", 8: "GPE_ENOTREADY"}
 
-EXPORTS = ["gpe_plan_create", "gpe_plan_destroy", "gpe_step_real", "gpe_step_real_host", "gpe_step_imag",
+EXPORTS = ["gpe_plan_create", "gpe_plan_destroy", "gpe_step_real", "gpe_step_real_host", "gpe_step_real_trap",
+           "gpe_step_imag",
            "gpe_norm_energy", "gpe_rms_size", "gpe_spectrum_nshells", "gpe_spectrum", "gpe_last_error",
            "gpe_trace_enable", "gpe_trace_count", "gpe_trace_read", "gpe_norm_energy_noalloc",
            "gpe_batch_create", "gpe_batch_destroy", "gpe_batch_step_real", "gpe_batch_norm_energy",
@@ -101,6 +102,7 @@ def lib():
         L.gpe_plan_create.argtypes = [ctypes.POINTER(gpe_plan_desc), vp, ctypes.POINTER(vp)]
         L.gpe_plan_destroy.argtypes = [vp]
         L.gpe_step_real.argtypes = [vp, vp, i64]
+        L.gpe_step_real_trap.argtypes = [vp, vp, i64, dp]
         L.gpe_step_real_host.argtypes = [vp, vp, i64]
         L.gpe_step_imag.argtypes = [vp, vp, i64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                     ctypes.POINTER(i64), dp]
@@ -163,6 +165,17 @@ def gpe_plan_destroy(plan):
 
 def gpe_step_real(plan, psi_ptr, nsteps):
     _check(lib().gpe_step_real(plan, ctypes.c_void_p(psi_ptr), int(nsteps)))
+
+
+def gpe_step_real_trap(plan, psi_ptr, gamma_t):
+    """gamma_t: array (nsteps + 1, ndim) of trap frequencies at the time levels."""
+    g = np.ascontiguousarray(gamma_t, dtype=np.float64)
+    if g.ndim != 2 or g.shape[0] < 1 or g.shape[1] < 1 or g.shape[1] > 3:
+        raise ValueError("gamma_t must have shape (nsteps + 1, ndim)")
+    g3 = np.zeros((g.shape[0], 3))
+    g3[:, :g.shape[1]] = g
+    _check(lib().gpe_step_real_trap(plan, ctypes.c_void_p(psi_ptr), int(g.shape[0] - 1),
+                                    g3.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
 
 
 def gpe_step_real_host(plan, psi_host_ptr, nsteps):
@@ -333,6 +346,10 @@ class Plan:
 
     def step_real(self, psi, nsteps):
         gpe_step_real(self._h, self._ptr(psi), nsteps)
+        return psi
+
+    def step_real_trap(self, psi, gamma_t):
+        gpe_step_real_trap(self._h, self._ptr(psi), gamma_t)
         return psi
 
     def step_imag(self, psi, max_steps, target_norm=1.0, etol=0.0, check_every=1):

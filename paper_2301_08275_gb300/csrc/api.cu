@@ -122,6 +122,9 @@ struct gpe_plan {
     int tx_extra = 0;                       // GPE_OPT_TEST_STALL_COPIES
     bool generic_passes = false;            // GPE_OPT_GENERIC_PASSES
     bool no_dither = false;                 // GPE_OPT_NO_DITHER
+    // trap tables of one time level (gpe_step_real_trap), allocated on first use
+    void *sched[3] = {nullptr, nullptr, nullptr};
+    void *sched_last = nullptr;
 };
 
 static gpe_status check_err(gpe_plan *p);
@@ -721,10 +724,61 @@ static void set_dither(PassArgs &k, double phi)
     k.dk[3] = (float)(wy - (double)hy);
 }
 
-static gpe_status step_real_dev(gpe_plan *p, void *psi, int64_t nsteps)
+// Trap tables of time level `lev` of a schedule (rows of three gamma) for a
+// nonlinear substep of length c dt, written into dst[a] for every instance.
+static gpe_status trap_level(gpe_plan *p, void *const *dst, const double *gamma_t, int64_t lev, double c)
+{
+    double gm[3] = {0, 0, 0};
+    for (int a = 0; a < p->ndim; ++a) gm[a] = gamma_t[3 * lev + a];
+    cudaError_t e = launch_trap_level(p->prec == GPE_C64 ? 0 : 1, dst, p->ndim, p->n, p->lo, p->h, gm, c * p->dt,
+                                      p->batch, p->st);
+    if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("trap tables: ") + cudaGetErrorString(e));
+    return GPE_OK;
+}
+static void use_sched(const gpe_plan *p, PassArgs &a)
+{
+    const int axis = a.axis;
+    const int o0 = axis == 0 ? 1 : 0, o1 = axis == 2 ? 1 : 2;
+    a.vt_ax = p->sched[axis];
+    a.vt_o0 = o0 < p->ndim ? p->sched[o0] : nullptr;
+    a.vt_o1 = o1 < p->ndim ? p->sched[o1] : nullptr;
+}
+
+// nsteps real-time steps; with gamma_t (nsteps + 1 rows of three trap
+// frequencies) the harmonic trap follows that schedule instead of the plan's
+// static trap: the nonlinear half-steps next to time level n use gamma_t row n.
+static gpe_status step_real_dev(gpe_plan *p, void *psi, int64_t nsteps, const double *gamma_t = nullptr)
 {
     if (nsteps == 0) return GPE_OK;
     const int64_t B = active_count(p);
+    if (p->ndim == 1 && gamma_t) {
+        // one on-chip launch per step, with the trap of both of its time levels
+        for (int64_t s = 0; s < nsteps; ++s) {
+            GPE_TRY(trap_level(p, p->sched, gamma_t, s, 0.5));
+            GPE_TRY(trap_level(p, &p->sched_last, gamma_t, s + 1, 0.5));
+            Line1DArgs l;
+            memset(&l, 0, sizeof(l));
+            l.psi = psi;
+            l.batch = B;
+            l.n = (int)p->n[0];
+            l.nsteps = 1;
+            l.tw = p->tw[0];
+            l.kt = p->kt[0];
+            l.vh = p->sched[0];
+            l.vh_last = p->sched_last;
+            l.g = p->g_dev;
+            l.dt = p->dt;
+            l.err = p->err;
+            if (p->cur_count > 0) {
+                l.inst_ptr = p->cur_ptrs;
+                l.slot_of = p->cur_slots;
+            }
+            TraceScope ts(p, "line1d" + std::to_string(l.n) + ":real");
+            cudaError_t e = launch_line1d(p->prec, l, p->st);
+            if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("1D launch: ") + cudaGetErrorString(e));
+        }
+        return GPE_OK;
+    }
     if (p->ndim == 1) {
         const int64_t chunk = 1 << 16;
         for (int64_t done = 0; done < nsteps; done += chunk) {
@@ -756,6 +810,10 @@ static gpe_status step_real_dev(gpe_plan *p, void *psi, int64_t nsteps)
     PassArgs x0 = make_pass(p, 0, psi, psi, B);
     x0.op_pre = OP_NREAL;
     set_nreal(p, x0, false);
+    if (gamma_t) {
+        GPE_TRY(trap_level(p, p->sched, gamma_t, 0, 0.5));
+        use_sched(p, x0);
+    }
     x0.fft1 = -1;
     GPE_TRY(run(p, x0));
     if (p->ndim == 3) {
@@ -783,6 +841,10 @@ static gpe_status step_real_dev(gpe_plan *p, void *psi, int64_t nsteps)
         x.fft1 = +1;
         x.op_mid = OP_NREAL;
         set_nreal(p, x, !last);
+        if (gamma_t) {
+            GPE_TRY(trap_level(p, p->sched, gamma_t, s + 1, last ? 0.5 : 1.0));
+            use_sched(p, x);
+        }
         x.dphi = phi;
         x.fft2 = last ? 0 : -1;
         GPE_TRY(run(p, x));
@@ -793,6 +855,23 @@ static gpe_status step_real_dev(gpe_plan *p, void *psi, int64_t nsteps)
         }
     }
     return GPE_OK;
+}
+
+extern "C" gpe_status gpe_step_real_trap(gpe_plan *p, void *psi, int64_t nsteps, const double *gamma_host)
+{
+    GPE_TRY(check_psi(p, psi));
+    if (nsteps < 0) return fail(GPE_EINVAL, "nsteps must be >= 0");
+    if (!gamma_host) return fail(GPE_EINVAL, "gamma_host is NULL");
+    if (p->vsamp) return fail(GPE_EUNSUPPORTED, "a trap schedule replaces the potential: plans with V_host have none");
+    for (int64_t i = 0; i < 3 * (nsteps + 1); ++i)
+        if (!isfinite(gamma_host[i])) return fail(GPE_EINVAL, "trap frequencies must be finite");
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return fail(GPE_ECUDA, "cannot select the plan's device");
+    const size_t ce = p->prec == GPE_C64 ? sizeof(float4) : sizeof(double2);
+    for (int a = 0; a < p->ndim; ++a)
+        if (!p->sched[a]) GPE_TRY(dalloc(p, &p->sched[a], ce * (size_t)p->n[a] * (size_t)p->batch));
+    if (p->ndim == 1 && !p->sched_last) GPE_TRY(dalloc(p, &p->sched_last, ce * (size_t)p->n[0] * (size_t)p->batch));
+    return step_real_dev(p, psi, nsteps, gamma_host);
 }
 
 extern "C" gpe_status gpe_step_real(gpe_plan *p, void *psi, int64_t nsteps)
@@ -1262,7 +1341,8 @@ extern "C" gpe_status gpe_spectrum(gpe_plan *p, const void *psi, unsigned kinds,
     }
     const int nb = bin_blocks(sa);
     if (!p->hist || p->nshells < ns || p->hist_blocks < nb) {
-        GPE_TRY(dalloc(p, (void **)&p->hist, sizeof(double) * 2 * (size_t)ns * nb));
+        // block histograms, then the fixed-point total partials and scale
+        GPE_TRY(dalloc(p, (void **)&p->hist, sizeof(double) * (2 * (size_t)ns * nb + nb + 1)));
         GPE_TRY(dalloc(p, (void **)&p->spec_out, sizeof(double) * 2 * (size_t)ns));
         p->nshells = ns;
         p->hist_blocks = nb;
@@ -1275,9 +1355,11 @@ extern "C" gpe_status gpe_spectrum(gpe_plan *p, const void *psi, unsigned kinds,
         SpecArgs sb = sa;
         sb.split = split;
         sb.ncomp = ncomp;
-        cudaError_t e = launch_bin(sb, uh, ns, p->hist, nb, p->st);
+        double *aux = p->hist + 2 * (size_t)ns * nb;
+        cudaError_t e = launch_bin(sb, uh, ns, p->hist, nb, aux, p->st);
         if (e == cudaSuccess)
-            e = launch_hist_reduce(p->hist, nb, ns, p->dv / (double)p->N, p->spec_out, p->spec_out + ns, p->st);
+            e = launch_hist_reduce(p->hist, nb, ns, p->dv / (double)p->N, aux, p->spec_out, p->spec_out + ns,
+                                   p->st);
         if (e != cudaSuccess) return fail(GPE_ECUDA, cudaGetErrorString(e));
         GPE_CUDA(cudaMemcpyAsync(tmp.data(), p->spec_out, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost, p->st));
         GPE_CUDA(cudaStreamSynchronize(p->st));

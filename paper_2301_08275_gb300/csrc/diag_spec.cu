@@ -3,6 +3,8 @@
 #include <math.h>
 
 #include "fft_tile.cuh"
+#include <algorithm>
+
 #include "gpe_internal.h"
 
 namespace gpe {
@@ -152,14 +154,58 @@ __global__ void k_velocity(const SpecArgs s, const typename CT<R>::C *__restrict
 
 // Shell histogram of |u_i|^2 and |u_c|^2 (split) or of sum_a |u_a|^2 (slot 0)
 // over the k grid, one partial histogram per block (hist[block][2][nshells]).
+// Shell sums are accumulated in 64-bit fixed point so that they do not depend
+// on the order in which threads add (integer addition is associative): a
+// deterministic pre-pass sums |u|^2 over the field in a fixed tree order,
+// the scale is the power of two that maps that total below 2^62, and every
+// point's contribution is rounded to an integer multiple of 1/scale before
+// the (integer) atomic additions.  Rounding costs at most total * 2^-63 per
+// point; the errors are of either sign and far below the FP64 sums' own.
 template <typename R>
-__global__ void k_bin(const SpecArgs s, const typename CT<R>::C *__restrict__ u0, const typename CT<R>::C *__restrict__ u1,
-                      const typename CT<R>::C *__restrict__ u2, int64_t nshells, double *__restrict__ hist)
+__global__ void k_field_total(const SpecArgs s, const typename CT<R>::C *__restrict__ u0,
+                              const typename CT<R>::C *__restrict__ u1, const typename CT<R>::C *__restrict__ u2,
+                              double *__restrict__ partial)
 {
     using C = typename CT<R>::C;
-    extern __shared__ double sh[];   // [2][nshells]
-    for (int64_t i = threadIdx.x; i < 2 * nshells; i += blockDim.x) sh[i] = 0.0;
+    __shared__ double red[256];
+    const C *u[3] = {u0, u1, u2};
+    const int nc = s.split ? s.ndim : s.ncomp;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.N; i += (int64_t)gridDim.x * blockDim.x)
+        for (int a = 0; a < nc; ++a) {
+            const C v = u[a][i];
+            acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+        }
+    red[threadIdx.x] = acc;
     __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+// fixed-order sum of the block partials; scale = 2^(61 - ceil(log2 total))
+__global__ void k_fixed_scale(double *aux, int nblocks)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += aux[b];
+    int ex = 0;
+    frexp(t > 0.0 ? t : 1.0, &ex);               // t < 2^ex
+    aux[nblocks] = ldexp(1.0, 61 - ex);
+}
+
+template <typename R>
+__global__ void k_bin(const SpecArgs s, const typename CT<R>::C *__restrict__ u0, const typename CT<R>::C *__restrict__ u1,
+                      const typename CT<R>::C *__restrict__ u2, int64_t nshells, const double *__restrict__ scale_p,
+                      unsigned long long *__restrict__ hist)
+{
+    using C = typename CT<R>::C;
+    extern __shared__ unsigned long long shq[];   // [2][nshells]
+    for (int64_t i = threadIdx.x; i < 2 * nshells; i += blockDim.x) shq[i] = 0ull;
+    __syncthreads();
+    const double scale = *scale_p;
+    auto fx = [scale](double v) { return (unsigned long long)(v * scale + 0.5); };
     const C *u[3] = {u0, u1, u2};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.N; i += (int64_t)gridDim.x * blockDim.x) {
         double kv[3] = {0.0, 0.0, 0.0}, q2 = 0.0, k2 = 0.0;
@@ -180,7 +226,7 @@ __global__ void k_bin(const SpecArgs s, const typename CT<R>::C *__restrict__ u0
                 const C v = u[a][i];
                 et += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
             }
-            atomicAdd(&sh[sh_i], et);
+            atomicAdd(&shq[sh_i], fx(et));
             continue;
         }
         double ur[3] = {0, 0, 0}, ui[3] = {0, 0, 0}, kdr = 0.0, kdi = 0.0;
@@ -198,26 +244,26 @@ __global__ void k_bin(const SpecArgs s, const typename CT<R>::C *__restrict__ u0
             ec += cr * cr + ci * ci;
             ei += (ur[a] - cr) * (ur[a] - cr) + (ui[a] - ci) * (ui[a] - ci);
         }
-        atomicAdd(&sh[sh_i], ei);
-        atomicAdd(&sh[nshells + sh_i], ec);
+        atomicAdd(&shq[sh_i], fx(ei));
+        atomicAdd(&shq[nshells + sh_i], fx(ec));
     }
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < 2 * nshells; i += blockDim.x) hist[(int64_t)blockIdx.x * 2 * nshells + i] = sh[i];
+    for (int64_t i = threadIdx.x; i < 2 * nshells; i += blockDim.x) hist[(int64_t)blockIdx.x * 2 * nshells + i] = shq[i];
 }
-
-// out[shell] = 1/2 dV/N sum over blocks (in block order) of the partial histograms.
-__global__ void k_hist_reduce(const double *__restrict__ hist, int nblocks, int64_t nshells, double half_dv_over_n,
-                              double *__restrict__ out_inc, double *__restrict__ out_comp)
+__global__ void k_hist_reduce(const unsigned long long *__restrict__ hist, int nblocks, int64_t nshells,
+                              const double *__restrict__ scale_p, double half_dv_over_n, double *__restrict__ out_inc,
+                              double *__restrict__ out_comp)
 {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= nshells) return;
-    double a = 0.0, c = 0.0;
+    unsigned long long a = 0ull, c = 0ull;
     for (int b = 0; b < nblocks; ++b) {
         a += hist[(int64_t)b * 2 * nshells + s];
         c += hist[(int64_t)b * 2 * nshells + nshells + s];
     }
-    out_inc[s] = half_dv_over_n * a;
-    out_comp[s] = half_dv_over_n * c;
+    const double inv = 1.0 / *scale_p;            // a power of two: exact
+    out_inc[s] = half_dv_over_n * ((double)a * inv);
+    out_comp[s] = half_dv_over_n * ((double)c * inv);
 }
 
 static int grid_for(int64_t N)
@@ -252,30 +298,87 @@ cudaError_t launch_velocity(const SpecArgs &s, const void *psi, void *w, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin(const SpecArgs &s, void *const *uh, int64_t nshells, double *block_hist, int nblocks,
-                       cudaStream_t st)
+// Trap tables of one time level (see launch_trap_level): angles in double
+// precision from the same formula as the plan's static tables, split into
+// hi + lo floats for complex64.
+__global__ void k_trap_level(int prec, void *t0, void *t1, void *t2, int ndim, int64_t n0, int64_t n1, int64_t n2,
+                             double lo0, double lo1, double lo2, double h0, double h1, double h2, double g0, double g1,
+                             double g2, double c, int64_t batch)
 {
-    const size_t smem = sizeof(double) * 2 * (size_t)nshells;
+    const int64_t tot = n0 + (ndim > 1 ? n1 : 0) + (ndim > 2 ? n2 : 0);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot * batch;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = q / tot;
+        int64_t j = q - b * tot;
+        int a = 0;
+        if (j >= n0) {
+            j -= n0;
+            a = 1;
+            if (j >= n1) {
+                j -= n1;
+                a = 2;
+            }
+        }
+        const int64_t na = a == 0 ? n0 : (a == 1 ? n1 : n2);
+        const double x = (a == 0 ? lo0 : (a == 1 ? lo1 : lo2)) + (double)j * (a == 0 ? h0 : (a == 1 ? h1 : h2));
+        const double gm = a == 0 ? g0 : (a == 1 ? g1 : g2);
+        const double th = 0.5 * gm * gm * x * x * c;
+        const double sh = sin(0.5 * th);
+        const double wx = -2.0 * sh * sh, wy = -sin(th);
+        void *t = a == 0 ? t0 : (a == 1 ? t1 : t2);
+        if (prec == 0) {
+            const float hx = (float)wx, hy = (float)wy;
+            static_cast<float4 *>(t)[b * na + j] =
+                make_float4(hx, hy, (float)(wx - (double)hx), (float)(wy - (double)hy));
+        } else {
+            static_cast<double2 *>(t)[b * na + j] = make_double2(wx, wy);
+        }
+    }
+}
+
+cudaError_t launch_trap_level(int prec, void *const *tab, int ndim, const int64_t *n, const double *lo,
+                              const double *h, const double *gamma, double c, int64_t batch, cudaStream_t st)
+{
+    const int64_t tot = (n[0] + (ndim > 1 ? n[1] : 0) + (ndim > 2 ? n[2] : 0)) * batch;
+    const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 1024);
+    k_trap_level<<<blocks, 256, 0, st>>>(prec, tab[0], ndim > 1 ? tab[1] : nullptr, ndim > 2 ? tab[2] : nullptr, ndim,
+                                         n[0], ndim > 1 ? n[1] : 1, ndim > 2 ? n[2] : 1, lo[0], lo[1], lo[2], h[0], h[1],
+                                         h[2], gamma[0], gamma[1], gamma[2], c, batch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const SpecArgs &s, void *const *uh, int64_t nshells, double *block_hist, int nblocks,
+                       double *aux, cudaStream_t st)
+{
+    const size_t smem = sizeof(unsigned long long) * 2 * (size_t)nshells;
+    unsigned long long *hq = reinterpret_cast<unsigned long long *>(block_hist);
     cudaError_t e;
     if (s.prec == 0) {
+        k_field_total<float><<<nblocks, 256, 0, st>>>(s, (const float2 *)uh[0], (const float2 *)uh[1],
+                                                      (const float2 *)uh[2], aux);
+        k_fixed_scale<<<1, 32, 0, st>>>(aux, nblocks);
         e = cudaFuncSetAttribute(k_bin<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_bin<float><<<nblocks, 256, smem, st>>>(s, (const float2 *)uh[0], (const float2 *)uh[1],
-                                                 (const float2 *)uh[2], nshells, block_hist);
+                                                 (const float2 *)uh[2], nshells, aux + nblocks, hq);
     } else {
+        k_field_total<double><<<nblocks, 256, 0, st>>>(s, (const double2 *)uh[0], (const double2 *)uh[1],
+                                                       (const double2 *)uh[2], aux);
+        k_fixed_scale<<<1, 32, 0, st>>>(aux, nblocks);
         e = cudaFuncSetAttribute(k_bin<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_bin<double><<<nblocks, 256, smem, st>>>(s, (const double2 *)uh[0], (const double2 *)uh[1],
-                                                  (const double2 *)uh[2], nshells, block_hist);
+                                                  (const double2 *)uh[2], nshells, aux + nblocks, hq);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_hist_reduce(const double *block_hist, int nblocks, int64_t nshells, double dv_over_n,
-                               double *out_inc, double *out_comp, cudaStream_t st)
+                               const double *aux, double *out_inc, double *out_comp, cudaStream_t st)
 {
     const int nb = (int)((nshells + 127) / 128);
-    k_hist_reduce<<<nb, 128, 0, st>>>(block_hist, nblocks, nshells, 0.5 * dv_over_n, out_inc, out_comp);
+    k_hist_reduce<<<nb, 128, 0, st>>>(reinterpret_cast<const unsigned long long *>(block_hist), nblocks, nshells,
+                                      aux + nblocks, 0.5 * dv_over_n, out_inc, out_comp);
     return cudaGetLastError();
 }
 

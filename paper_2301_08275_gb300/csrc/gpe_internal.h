@@ -112,6 +112,7 @@ struct Line1DArgs {
     const void *tw;
     const void *kt;         // offsets exp(-i k^2 dt/2) - 1 (real time) or exp(-k^2 dt/2)/n (imag)
     const void *vh, *vf;    // offsets exp(-i V dt/2) - 1, exp(-i V dt) - 1 ([batch][n]) or NULL
+    const void *vh_last;    // optional: the last half-step's table instead of vh (time-dependent trap)
     const void *vi;         // real decay table (imag) or NULL
     const double *g;
     double dt;
@@ -121,6 +122,13 @@ struct Line1DArgs {
     const int *slot_of;     // optional: parameter/table slot of instance b
 };
 cudaError_t launch_line1d(int prec, const Line1DArgs &a, cudaStream_t st);
+
+// trap tables of one time level of a time-dependent harmonic trap (diag_spec.cu):
+// for every axis a < ndim and every instance, tab[a][b*n[a] + j] = exp(-i V_a c) - 1
+// with V_a = gamma[a]^2 x_j^2 / 2, x_j = lo[a] + j h[a] (float4 hi/lo pairs for
+// prec 0, double2 for prec 1)
+cudaError_t launch_trap_level(int prec, void *const *tab, int ndim, const int64_t *n, const double *lo,
+                              const double *h, const double *gamma, double c, int64_t batch, cudaStream_t st);
 
 // reductions and spectra (diag_spec.cu)
 cudaError_t launch_reduce_lines(const double *partials, int64_t lines_cap, int nq_first, int nq,
@@ -143,10 +151,10 @@ struct SpecArgs {
 };
 cudaError_t launch_deriv(const SpecArgs &s, const void *src, void *dst, int axis, cudaStream_t st);
 cudaError_t launch_velocity(const SpecArgs &s, const void *psi, void *w, cudaStream_t st);
-cudaError_t launch_bin(const SpecArgs &s, void *const *uh, int64_t nshells, double *block_hist,
-                       int nblocks, cudaStream_t st);
+cudaError_t launch_bin(const SpecArgs &s, void *const *uh, int64_t nshells, double *block_hist, int nblocks,
+                       double *aux, cudaStream_t st);
 cudaError_t launch_hist_reduce(const double *block_hist, int nblocks, int64_t nshells, double dv_over_n,
-                               double *out_inc, double *out_comp, cudaStream_t st);
+                               const double *aux, double *out_inc, double *out_comp, cudaStream_t st);
 int bin_blocks(const SpecArgs &s);
 
 }  // namespace gpe

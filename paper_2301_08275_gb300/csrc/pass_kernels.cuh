@@ -450,17 +450,15 @@ template <typename R, int N, bool ROWS> __host__ __device__ constexpr int pass_p
                                                                : Radix<N>::E;
 }
 
-// Shared layout of the transform exchanges.  Rows of the split tiles are
-// swizzled (see rows_split).  Strided tiles with 32 points per thread and
-// fewer than 16 lines swizzle too: the first pass writes points 32 apart from
-// lanes whose tl differ, which fall into the same banks when a point row
-// (L lines) is narrower than 128 bytes; the swizzle spreads them over the
-// row.  A tile staged by the copy engine arrives unswizzled and is read with
-// the plain index.
+// Shared layout of the transform exchanges: rows of the split tiles are
+// swizzled (see rows_split), strided tiles are not.  (Swizzling the 8-line
+// strided tiles of 32 points per thread removes the 4-way bank conflicts of
+// their first exchange, but with it the 512^3 y sweep ran at 0.475 ms
+// against 0.347 ms without.)  A tile staged by the copy engine is read
+// with the plain index.
 template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr bool pass_swizzle()
 {
-    return rows_split<R, N, ROWS, VAR>() ||
-           (!ROWS && pass_points_per_thread<R, N, ROWS>() == 32 && pick_lines<R, N, ROWS, VAR>() * (int)sizeof(R) * 2 < 128);
+    return rows_split<R, N, ROWS, VAR>();
 }
 template <typename R, int N, bool ROWS, int VAR>
 using PassTile = GTile<R, N, pick_lines<R, N, ROWS, VAR>(), lines_per_thread<R>(), pass_swizzle<R, N, ROWS, VAR>(),
@@ -481,11 +479,9 @@ template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr i
 {
     constexpr int nt = PassTile<R, N, ROWS, VAR>::NT;
     constexpr int want = 1024 / nt > 16 ? 16 : 1024 / nt;
-    // strided tiles of 32 points per thread: as many CTAs as the shared memory
-    // holds (registers are then capped accordingly: 3 CTAs of 128 threads,
-    // 170 registers)
-    constexpr bool wide = !ROWS && pass_points_per_thread<R, N, ROWS>() == 32;
-    constexpr int b = (rows_split<R, N, ROWS, VAR>() || wide) && want > 2 ? want : (nt > 512 ? 1 : 2);
+    // (strided tiles of 32 points per thread keep 2: capping their registers
+    // for a third CTA, 170, made the 512^3 y sweep slower, 0.347 -> 0.475 ms)
+    constexpr int b = rows_split<R, N, ROWS, VAR>() && want > 2 ? want : (nt > 512 ? 1 : 2);
     constexpr int fit = (int)(227 * 1024 / (pass_smem_base<R, N, ROWS, VAR>() + 1024));
     return b < fit ? b : (fit > 0 ? fit : 1);
 }
@@ -836,7 +832,7 @@ __global__ void __launch_bounds__(Tile<R, N, L, true>::NT) k_line1d(const Line1D
                 T::template fft<1>(v, sm, tl, l, tw);
                 const bool last = (st == a.nsteps - 1);
                 const R gc = last ? gh : gf;
-                const U *vt = last ? vh : vf;
+                const U *vt = last ? (a.vh_last ? static_cast<const U *>(a.vh_last) : vh) : vf;
                 R th[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) th[e] = gc * cabs2(v[e]);

@@ -489,8 +489,10 @@ def test_quantum_pressure_and_number_spectra_match_oracle(gpe, orc, prec):
     # (to 7e-11 in the oracle for this field: its Nyquist content is that small)
     assert abs(out[0, 0].sum() + out[1, 0].sum() + out[2, 0].sum() - e[1]) < (1e-9 if prec == "c128" else 1e-5) * e[1]
     only = p.spectrum(x, kinds=gpe.GPE_SPEC_QP)
-    # shells are accumulated with atomic adds, so repeated calls agree to rounding
-    assert only.shape == (1, 1, len(eq)) and np.allclose(only[0, 0], out[2, 0], rtol=1e-12, atol=0)
+    # shells are summed in fixed point: repeated calls give the same bits
+    assert only.shape == (1, 1, len(eq)) and np.array_equal(only[0, 0], out[2, 0])
+    again = p.spectrum(x, kinds=k)
+    assert np.array_equal(again, out)
     p.close()
 
 
