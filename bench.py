@@ -431,6 +431,19 @@ def run_ours(args, key, wl):
         del ref_state
 
     cufft = cufft_reference(spec, psi) if (spec.ndim >= 2 and rank == 0) else None
+    batched = serving = None
+    if rank == 0 and ws == 1 and key == "tg512" and not args.no_sub:
+        # the batched and serving configurations, short runs of each with their
+        # sequential baselines (the full runs: --workload batched / serving)
+        batched = batched_record(512, 100, 3)
+        sus = serving_record(200, 10.0, args.max_active, args.max2d, args.max3d)
+        over = serving_record(200, 200.0, args.max_active, args.max2d, args.max3d, sequential=False)
+        seq = sus.pop("sequential")
+        # the same 200 requests (seed 0) each time; throughput compared where the
+        # server is saturated, latency where the arrivals are sustainable
+        serving = {"sustainable": sus, "overload": over, "sequential": seq,
+                   "throughput_vs_sequential": over["updates_per_s"] / seq["updates_per_s"],
+                   "p50_vs_sequential": sus["p50_s"] / seq["p50_s"], "p99_vs_sequential": sus["p99_s"] / seq["p99_s"]}
     nrm = plan.norm_energy(psi)[0]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -443,7 +456,7 @@ def run_ours(args, key, wl):
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "tiles": tiles, "norm_after": float(nrm[0])},
             "roofline": roofline, "cpu_baseline": cpu, "parity": parity, "e2e": e2e, "cufft_reference": cufft,
-            "clocks": clk.summary(), "gpu_launches": launches}
+            "clocks": clk.summary(), "gpu_launches": launches, "batched": batched, "serving": serving}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -453,17 +466,15 @@ def run_ours(args, key, wl):
     return 0
 
 
-def run_batched(args):
-    """512 uneven 2D instances (64^2..512^2, g in [0,1000], traps gamma in [1,4]),
-    500 real-time steps: one graph-captured batch call versus sequential
-    per-instance stepping with the same kernels."""
+def batched_record(count, steps, warmup):
+    """`count` uneven 2D instances (64^2..512^2, g in [0,1000], traps gamma in
+    [1,4]), `steps` real-time steps: one graph-captured batch call against
+    sequential per-instance stepping with the same kernels, one plan per
+    instance, one instance after another."""
     import torch
     import paper_2301_08275_gb300 as gpe
     gpe.build()
-    torch.cuda.set_device(0)
-    count = args.instances
     items = gi.batched_specs(count=count, seed=0)
-    steps = args.steps
     stream = torch.cuda.Stream()
     xs = [torch.from_numpy(psi.astype(np.complex64)).cuda() for _, psi in items]
     descs = [gpe.make_desc(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma, prec=gpe.GPE_C64)[0]
@@ -471,7 +482,7 @@ def run_batched(args):
     torch.cuda.synchronize()
     b = gpe.gpe_batch_create(descs, stream.cuda_stream)
     ptrs = [x.data_ptr() for x in xs]
-    gpe.gpe_batch_step_real(b, ptrs, args.warmup, True)
+    gpe.gpe_batch_step_real(b, ptrs, warmup, True)
     gpe.gpe_batch_step_real(b, ptrs, steps, True)          # capture
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -481,11 +492,10 @@ def run_batched(args):
     torch.cuda.synchronize()
     t_batch = ev0.elapsed_time(ev1) / 1e3
     pts = sum(sp.N for sp, _ in items)
-    # sequential: one plan per instance, stepped one after another
     plans = [gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma, prec=gpe.GPE_C64, stream=stream)
              for sp, _ in items]
     for p, x in zip(plans, xs):
-        p.step_real(x, args.warmup)
+        p.step_real(x, warmup)
     torch.cuda.synchronize()
     ev0.record(stream)
     for p, x in zip(plans, xs):
@@ -494,38 +504,50 @@ def run_batched(args):
     torch.cuda.synchronize()
     t_seq = ev0.elapsed_time(ev1) / 1e3
     e = gpe.gpe_batch_norm_energy(b, ptrs)
-    line = {"metric": "batched TSSP grid-point updates/s", "value": pts * steps / t_batch, "unit": UNIT,
-            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": t_batch / steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "%d uneven 2D instances 64^2..512^2, [-12,12)^2, g~U[0,1000], gamma~U[1,4], "
-                                   "complex64" % count, "groups": gpe.gpe_batch_groups(b), "points": pts},
-            "sequential": {"value": pts * steps / t_seq, "ms_per_step": t_seq / steps * 1e3,
-                           "how": "one plan per instance, gpe_step_real(%d) one after another" % steps},
-            "speedup_vs_sequential": t_seq / t_batch, "finite": bool(np.all(np.isfinite(e)))}
-    print(json.dumps(line), flush=True)
+    rec = {"value": pts * steps / t_batch, "unit": UNIT, "instances": count, "steps": steps, "points": pts,
+           "ms_per_step": t_batch / steps * 1e3, "groups": gpe.gpe_batch_groups(b),
+           "sequential": {"value": pts * steps / t_seq, "ms_per_step": t_seq / steps * 1e3,
+                          "how": "one plan per instance, gpe_step_real(%d) one instance after another" % steps},
+           "speedup_vs_sequential": t_seq / t_batch, "finite": bool(np.all(np.isfinite(e))),
+           "workload": "%d uneven 2D instances 64^2..512^2, [-12,12)^2, g~U[0,1000], gamma~U[1,4], complex64"
+                       % count}
+    for p in plans:
+        p.close()
     gpe.gpe_batch_destroy(b)
+    del xs
+    torch.cuda.empty_cache()
+    return rec
+
+
+def run_batched(args):
+    import torch
+    torch.cuda.set_device(0)
+    r = batched_record(args.instances, args.steps, args.warmup)
+    line = {"metric": "batched TSSP grid-point updates/s", "value": r["value"], "unit": UNIT,
+            "n_gpus": 1, "steps": r["steps"], "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": r["workload"], "groups": r["groups"], "points": r["points"]},
+            "sequential": r["sequential"], "speedup_vs_sequential": r["speedup_vs_sequential"],
+            "finite": r["finite"]}
+    print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serving(args):
-    """Poisson stream (mean 200 requests/s) of mixed 1D/2D/3D solves, real and
-    imaginary time, through the request server; p50/p99 latency, aggregate
-    grid-point updates/s and admitted concurrency.  Initial states come from a
-    pool of four per grid shape built before the clock starts, so that the
-    submitting thread keeps to the arrival schedule; a second thread polls the
-    tickets in order and drops each result as it is read."""
-    import threading
-    import torch
-    import paper_2301_08275_gb300 as gpe
-    gpe.build()
-    torch.cuda.set_device(0)
-    items = gi.request_stream(count=args.requests, rate=200.0, seed=0, max2d=args.max2d, max3d=args.max3d)
+def _request_pool(items):
     pool = {}
     for it in items:
         lst = pool.setdefault(tuple(it["spec"].n), [])
         if len(lst) < 4:
             lst.append(gi.harmonic_gaussian(it["spec"], seed=it["seed"], noise=0.01).astype(np.complex64))
-    srv = gpe.gpe_server_create(150 * 10 ** 9, max_active=args.max_active, chunk_steps=64)
+    return pool
+
+
+def serve_stream(items, max_active, pool):
+    """Submit `items` to the request server on their arrival schedule; a second
+    thread polls the tickets in order.  Returns latencies, updates and stats."""
+    import threading
+    import paper_2301_08275_gb300 as gpe
+    srv = gpe.gpe_server_create(150 * 10 ** 9, max_active=max_active, chunk_steps=64)
     n = len(items)
     tickets, results = [None] * n, [None] * n
     submitted = threading.Semaphore(0)
@@ -574,12 +596,80 @@ def run_serving(args):
     lat = np.array(lat)
     act = np.array([a for _, a, _ in samples]) if samples else np.zeros(1)
     que = np.array([q for q, _, _ in samples]) if samples else np.zeros(1)
+    return {"p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "updates_per_s": upd / wall, "requests": n, "failed": fails, "wall_s": wall,
+            "arrival_span_s": items[-1]["t"] if items else 0.0, "max_submit_lag_s": lag,
+            "active_mean": float(act.mean()), "active_max": int(act.max()), "queued_max": int(que.max())}
+
+
+def serve_sequential(items, pool):
+    """The same requests with plain single-instance stepping, one after another
+    (a plan per request, gpe_step_real or gpe_step_imag with the same rule),
+    each timed alone; latencies follow a first-come first-served queue on the
+    same arrival times."""
+    import torch
+    import paper_2301_08275_gb300 as gpe
+    service, upd = [], 0.0
+    for i, it in enumerate(items):
+        sp = it["spec"]
+        t0 = time.perf_counter()
+        p = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma, prec=gpe.GPE_C64)
+        lst = pool[tuple(sp.n)]
+        x = torch.from_numpy(lst[i % len(lst)]).cuda()
+        if it["mode"] == "imag":
+            done, _ = p.step_imag(x, it["steps"], etol=it["etol"], check_every=50)
+        else:
+            p.step_real(x, it["steps"])
+            done = it["steps"]
+        x.cpu()
+        p.close()
+        service.append(time.perf_counter() - t0)
+        upd += sp.N * done
+    finish, lat = 0.0, []
+    for it, s_ in zip(items, service):
+        start = max(it["t"], finish)
+        finish = start + s_
+        lat.append(finish - it["t"])
+    lat = np.array(lat)
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "updates_per_s": upd / sum(service), "busy_s": sum(service),
+            "how": "each request alone on a fresh plan (upload, steps, download), one after another; latency of a "
+                   "first-come first-served queue on the same arrival times"}
+
+
+def serving_record(requests, rate, max_active, max2d, max3d, sequential=True):
+    """Poisson stream of mixed 1D/2D/3D solves through the request server, at
+    one arrival rate, and (optionally) the same stream stepped sequentially."""
+    import torch
+    import paper_2301_08275_gb300 as gpe
+    gpe.build()
+    items = gi.request_stream(count=requests, rate=rate, seed=0, max2d=max2d, max3d=max3d)
+    pool = _request_pool(items)
+    rec = serve_stream(items, max_active, pool)
+    rec["rate_per_s"] = rate
+    if sequential:
+        rec["sequential"] = serve_sequential(items, pool)
+    torch.cuda.empty_cache()
+    return rec
+
+
+def run_serving(args):
+    """Poisson stream (mean 200 requests/s) of mixed 1D/2D/3D solves, real and
+    imaginary time, through the request server; p50/p99 latency, aggregate
+    grid-point updates/s and admitted concurrency.  Initial states come from a
+    pool of four per grid shape built before the clock starts, so that the
+    submitting thread keeps to the arrival schedule; a second thread polls the
+    tickets in order and drops each result as it is read."""
+    import torch
+    torch.cuda.set_device(0)
+    r = serving_record(args.requests, 200.0, args.max_active, args.max2d, args.max3d, sequential=False)
     line = {"metric": "served GPE solves: p50/p99 latency and aggregate updates/s",
-            "value": float(np.percentile(lat, 50)) if len(lat) else None, "unit": "s (p50 latency)",
-            "p99_s": float(np.percentile(lat, 99)) if len(lat) else None, "updates_per_s": upd / wall,
-            "requests": n, "failed": fails, "wall_s": wall, "arrival_span_s": items[-1]["t"] if items else 0.0,
-            "max_submit_lag_s": lag, "active_mean": float(act.mean()), "active_max": int(act.max()),
-            "queued_max": int(que.max()), "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "f32",
+            "value": r["p50_s"], "unit": "s (p50 latency)", "p99_s": r["p99_s"], "updates_per_s": r["updates_per_s"],
+            "requests": r["requests"], "failed": r["failed"], "wall_s": r["wall_s"],
+            "arrival_span_s": r["arrival_span_s"], "max_submit_lag_s": r["max_submit_lag_s"],
+            "active_mean": r["active_mean"], "active_max": r["active_max"], "queued_max": r["queued_max"],
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "f32",
             "config": {"workload": "Poisson 200 req/s; 1D 4096, 2D 256^2..%d^2, 3D 64^3..%d^3; real 100-2000 steps "
                                    "or imaginary time to |dE|<1e-9 (checked every 50 steps); budget 150 GB; "
                                    "initial states from a pool of 4 per shape" % (args.max2d, args.max3d),
@@ -842,6 +932,7 @@ def main():
     ap.add_argument("--max2d", type=int, default=2048, help="serving: largest 2D grid side")
     ap.add_argument("--max3d", type=int, default=256, help="serving: largest 3D grid side")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-sub", action="store_true", help="skip the batched and serving sub-records")
     ap.add_argument("--grid", default=None,
                     help="override the workload grid, e.g. 512,512,128 (profiling cases; same box and parameters)")
     args = ap.parse_args()
