@@ -193,6 +193,10 @@ def pass_flops_per_point(kind):
     as 'y1024:F-KR-I': 5 log2(n) per n-point complex transform (the usual
     radix-2 count) and 6 per pointwise complex multiplication substep."""
     head, prog = kind.split(":", 1)
+    if head.startswith("line1d"):
+        # the on-chip 1D kernel: every step two transforms and two pointwise substeps
+        n = int(head[len("line1d"):])
+        return 2.0 * 5.0 * math.log2(n) + 2.0 * 6.0
     n = int("".join(ch for ch in head if ch.isdigit()))
     toks = prog.split("-")
     ffts = sum(1 for t in toks if t in ("F", "I"))
@@ -330,6 +334,69 @@ def cufft_reference(spec, psi, steps=10):
                     "a reference point beside the library, never called by it"}
 
 
+def config_record(key, steps=None):
+    """One of the smaller configurations at its full length on an autotuned
+    plan: updates/s from CUDA events, the per-kernel split from a traced
+    repeat, and the roofline of the dominant kernel (HBM for complex64,
+    FP64 arithmetic for complex128).  Turbulence runs read their spectra every
+    200 steps inside the timed region, as the full workload does."""
+    import torch
+    import paper_2301_08275_gb300 as gpe
+    wl = WORKLOADS[key]
+    spec = wl["spec"]
+    steps = steps or wl["length"]
+    prec = gpe.GPE_C64 if wl["prec"] == "c64" else gpe.GPE_C128
+    stream = torch.cuda.Stream()
+    plan = gpe.Plan(spec.n, spec.lo, spec.length, g=spec.g, dt=spec.dt, gamma=spec.gamma[: spec.ndim],
+                    prec=prec, stream=stream)
+    dt = np.complex64 if prec == gpe.GPE_C64 else np.complex128
+    x = torch.from_numpy(np.ascontiguousarray(initial_state(key, spec)).astype(dt)).cuda()
+    torch.cuda.synchronize()
+    tiles = plan.autotune(x, reps=3) if spec.ndim > 1 else None
+    w = x.clone()
+    plan.step_real(w, 5)
+    del w
+    n0 = plan.norm_energy(x)[0][0]
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    se = wl.get("spectra_every")
+    if se:
+        for s0 in range(0, steps, se):
+            plan.step_real(x, min(se, steps - s0))
+            plan.spectrum(x)
+    else:
+        plan.step_real(x, steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    n1 = plan.norm_energy(x)[0][0]
+    plan.trace(True)
+    plan.step_real(x, min(steps, 200))
+    tr = plan.trace_read()
+    plan.trace(False)
+    kind, (cnt, tot) = max(tr.items(), key=lambda kv: kv[1][1])
+    kernels = {k: {"launches": c, "avg_ms": t / c} for k, (c, t) in tr.items()}
+    state_bytes = spec.N * (8 if prec == gpe.GPE_C64 else 16)
+    if prec == gpe.GPE_C128:
+        # a 1D launch runs every step of the call: its flops per launch scale with them
+        per_launch = spec.N * (min(steps, 200) if kind.startswith("line1d") else 1)
+        roof = alu_roofline(gpe, stream, kind, tot / cnt, per_launch, kernels)
+    else:
+        peak, src = measured_peaks()
+        ach = 2.0 * state_bytes / (tot / cnt / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "kernel": kind,
+                "kernel_avg_ms": tot / cnt, "peak_source": src, "kernels": kernels}
+        if state_bytes < 100e6:
+            roof["l2_resident"] = "the %.0f MiB state stays in L2 between launches (latency bound)" % (
+                state_bytes / 2 ** 20)
+    plan.close()
+    return {"workload": wl["name"], "value": spec.N * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
+            "ms_per_step": ms / steps, "us_per_step": 1e3 * ms / steps, "dtype": wl["prec"], "tiles": tiles,
+            "norm_drift": float(abs(n1 / n0 - 1.0)), "roofline": roof,
+            "note": "timed region includes the spectra every %d steps" % se if se else None}
+
+
 def run_ours(args, key, wl):
     import torch
     import paper_2301_08275_gb300 as gpe
@@ -351,7 +418,13 @@ def run_ours(args, key, wl):
     psi = torch.from_numpy(np.ascontiguousarray(psi0).astype(np.complex64 if prec == gpe.GPE_C64 else np.complex128)).to(dev)
     del psi0
     torch.cuda.synchronize(dev)
-    tiles = plan.autotune(psi, reps=3)     # tile shapes / staging timed on this grid, before any timed region
+    if args.tiles:
+        # fixed tile shapes (profiling: no tuner launches before the timed region)
+        for opt, v in zip((gpe.GPE_OPT_TILE_X, gpe.GPE_OPT_TILE_Y, gpe.GPE_OPT_TILE_Z), args.tiles.split(",")):
+            plan.set_option(opt, int(v))
+        tiles = {"fixed": args.tiles}
+    else:
+        tiles = plan.autotune(psi, reps=3)     # tile shapes / staging timed on this grid, before any timed region
 
     def barrier():
         if ws > 1:
@@ -431,8 +504,15 @@ def run_ours(args, key, wl):
         del ref_state
 
     cufft = cufft_reference(spec, psi) if (spec.ndim >= 2 and rank == 0) else None
-    batched = serving = None
+    batched = serving = configs = None
     if rank == 0 and ws == 1 and key == "tg512" and not args.no_sub:
+        # the other configurations at their full lengths (oracle parity of each
+        # at full length is in the -m gpu tests)
+        configs = {k: config_record(k) for k in ("line256", "turb1024", "turb1024c128")}
+        tr_rec = trap_record(imag_max=20000, steps=2000, warmup=3)
+        tr_rec.pop("_plan").close()
+        tr_rec.pop("_psi")
+        configs["trap256"] = tr_rec
         # the batched and serving configurations, short runs of each with their
         # sequential baselines (the full runs: --workload batched / serving)
         batched = batched_record(512, 100, 3)
@@ -456,7 +536,8 @@ def run_ours(args, key, wl):
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "tiles": tiles, "norm_after": float(nrm[0])},
             "roofline": roofline, "cpu_baseline": cpu, "parity": parity, "e2e": e2e, "cufft_reference": cufft,
-            "clocks": clk.summary(), "gpu_launches": launches, "batched": batched, "serving": serving}
+            "clocks": clk.summary(), "gpu_launches": launches, "configs": configs, "batched": batched,
+            "serving": serving}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -678,57 +759,41 @@ def run_serving(args):
     return 0
 
 
-def run_trap(args):
+def trap_record(imag_max=20000, steps=2000, warmup=3, grid=None, seed=0, stream=None, barrier=None):
     """3D anisotropic trap 256^3, gamma = (1, 2, 4), g = 200, box [-8, 8)^3: the ground
     state by imaginary time (renormalised every step) until |dE| < 1e-10 between
     checks every 16 steps (complex64 down to 1e-6, where its energy stops
-    resolving, then complex128), then the trap frequencies doubled and
-    `--steps` real-time steps with the rms sizes read back every 10 steps.
-    value = grid-point updates/s of the real-time phase including the rms
-    reads; the imaginary-time phase is reported beside it."""
+    resolving, then complex128), then the trap frequencies doubled and `steps`
+    real-time steps with the rms sizes read back every 10 steps.  value =
+    grid-point updates/s of the real-time phase including the rms reads; the
+    imaginary-time phase is reported beside it."""
     import torch
     import paper_2301_08275_gb300 as gpe
-    ws, rank, local = dist_setup()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    gpe.build()
     sp = gi.CONFIG_3D_TRAP
-    if args.grid:
-        sp = gi.Spec(n=tuple(int(v) for v in args.grid.split(",")), lo=sp.lo, length=sp.length, g=sp.g,
-                     dt=sp.dt, gamma=sp.gamma)
+    if grid:
+        sp = gi.Spec(n=tuple(grid), lo=sp.lo, length=sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma)
     quench = tuple(2.0 * g for g in sp.gamma)
-    stream = torch.cuda.Stream(device=dev)
+    stream = stream or torch.cuda.Stream()
+    barrier = barrier or torch.cuda.synchronize
     pi = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma, prec=gpe.GPE_C64, stream=stream)
     pr = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=quench, prec=gpe.GPE_C64, stream=stream)
-    psi = torch.from_numpy(gi.harmonic_gaussian(sp, seed=rank, noise=0.01).astype(np.complex64)).to(dev)
-    torch.cuda.synchronize(dev)
+    psi = torch.from_numpy(gi.harmonic_gaussian(sp, seed=seed, noise=0.01).astype(np.complex64)).cuda()
+    torch.cuda.synchronize()
     tiles_i = pi.autotune(psi, reps=3)
     tiles_r = pr.autotune(psi, reps=3)
-
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-
     # warm-up on copies (the timed phases start from the real initial state)
     w = psi.clone()
-    pi.step_imag(w, max(3, args.warmup), etol=0.0, check_every=max(3, args.warmup))
-    pr.step_real(w, max(3, args.warmup))
+    pi.step_imag(w, max(3, warmup), etol=0.0, check_every=max(3, warmup))
+    pr.step_real(w, max(3, warmup))
     pr.rms_size(w)
     del w
     barrier()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-    # ground state in two stages: complex64 until |dE| < 1e-6 (its energy
-    # resolves no further), then complex128 until |dE| < 1e-10
     ev[0].record(stream)
-    done, e64 = pi.step_imag(psi, args.imag_max, target_norm=1.0, etol=1e-6, check_every=16)
+    done, e64 = pi.step_imag(psi, imag_max, target_norm=1.0, etol=1e-6, check_every=16)
     ev[1].record(stream)
     barrier()
-    ms_imag = max_over_ranks(ev[0].elapsed_time(ev[1]), dev)
+    ms_imag = ev[0].elapsed_time(ev[1])
     p128 = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma, prec=gpe.GPE_C128, stream=stream)
     psi128 = psi.to(torch.complex128)
     w = psi128.clone()
@@ -736,27 +801,24 @@ def run_trap(args):
     del w
     barrier()
     ev[4].record(stream)
-    done128, e_ground = p128.step_imag(psi128, args.imag_max, target_norm=1.0, etol=1e-10, check_every=16)
+    done128, e_ground = p128.step_imag(psi128, imag_max, target_norm=1.0, etol=1e-10, check_every=16)
     ev[5].record(stream)
     barrier()
-    ms_imag128 = max_over_ranks(ev[4].elapsed_time(ev[5]), dev)
+    ms_imag128 = ev[4].elapsed_time(ev[5])
     ground = p128.norm_energy(psi128)[0]
     sig0 = p128.rms_size(psi128)[0]
     p128.close()
     psi.copy_(psi128.to(torch.complex64))
     del psi128
     sig = []
-    with ClockSampler(local) as clk:
-        barrier()
-        ev[2].record(stream)
-        for s0 in range(0, args.steps, 10):
-            pr.step_real(psi, min(10, args.steps - s0))
-            sig.append(pr.rms_size(psi)[0])
-        ev[3].record(stream)
-        barrier()
-    ms_real = max_over_ranks(ev[2].elapsed_time(ev[3]), dev)
-    value = ws * sp.N * args.steps / (ms_real / 1e3)
-    # per-kernel timing of the real-time step, traced
+    barrier()
+    ev[2].record(stream)
+    for s0 in range(0, steps, 10):
+        pr.step_real(psi, min(10, steps - s0))
+        sig.append(pr.rms_size(psi)[0])
+    ev[3].record(stream)
+    barrier()
+    ms_real = ev[2].elapsed_time(ev[3])
     pr.trace(True)
     barrier()
     pr.step_real(psi, 100)
@@ -772,7 +834,51 @@ def run_trap(args):
                 "traffic": None, "kernel": kind, "kernel_avg_ms": avg_ms, "bytes_per_launch": bpl,
                 "peak_source": peak_src,
                 "kernels": {k: {"launches": c, "avg_ms": t / c} for k, (c, t) in tr.items()}}
-    # end to end: host buffer in and out every step
+    rec = {"value": sp.N * steps / (ms_real / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms_real / steps,
+           "workload": "3D trap %s, gamma=(1,2,4) -> (2,4,8) after the ground state, g=200, box [-8,8)^3, dt=1e-3, "
+                       "complex64 bulk / FP64 tables and reductions; rms sizes read back every 10 real-time steps"
+                       % "x".join(map(str, sp.n)),
+           "grid": list(sp.n), "tiles_imag": tiles_i, "tiles_real": tiles_r,
+           "imag": {"c64": {"steps": int(done), "etol": 1e-6, "ms_per_step": ms_imag / max(1, done),
+                            "updates_per_s": sp.N * done / (ms_imag / 1e3), "E": float(e64[0])},
+                    "c128": {"steps": int(done128), "etol": 1e-10, "ms_per_step": ms_imag128 / max(1, done128),
+                             "updates_per_s": sp.N * done128 / (ms_imag128 / 1e3)},
+                    "converged": bool(done128 < imag_max), "E": float(e_ground[0]),
+                    "mu": float(ground[5]), "sigma": [float(v) for v in sig0[:3]], "r_rms": float(sig0[3])},
+           "sigma_final": [float(v) for v in sig[-1][:3]] if sig else None, "roofline": roofline,
+           "gpu_launches": int(sum(c for c, _ in tr.values()))}
+    rec["_plan"], rec["_psi"] = pr, psi
+    return rec
+
+
+def run_trap(args):
+    """The trap workload (trap_record) as its own bench line, with the host-buffer
+    end-to-end rate and the CPU oracle beside it."""
+    import torch
+    import paper_2301_08275_gb300 as gpe
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gpe.build()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    stream = torch.cuda.Stream(device=dev)
+    grid = tuple(int(v) for v in args.grid.split(",")) if args.grid else None
+    with ClockSampler(local) as clk:
+        r = trap_record(args.imag_max, args.steps, args.warmup, grid=grid, seed=rank, stream=stream, barrier=barrier)
+    pr, psi = r.pop("_plan"), r.pop("_psi")
+    ms_real = max_over_ranks(r["ms_per_step"] * args.steps, dev)
+    sp_n = r["grid"]
+    N = int(np.prod(sp_n))
+    value = ws * N * args.steps / (ms_real / 1e3)
     e2e_steps = 10
     host = torch.empty(psi.shape, dtype=torch.complex64, pin_memory=True)
     host.copy_(psi.cpu())
@@ -782,16 +888,16 @@ def run_trap(args):
     for _ in range(e2e_steps):
         pr.step_real_host(hnp, 1)
     el = max_over_ranks(time.perf_counter() - t0, dev)
-    state_bytes = sp.N * 8
-    e2e = {"value": ws * sp.N * e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
-           "d2h_bytes_per_step": state_bytes, "steps": e2e_steps,
-           "api": "gpe_step_real_host (1 step per call, pinned host buffer)"}
+    e2e = {"value": ws * N * e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8,
+           "steps": e2e_steps, "api": "gpe_step_real_host (1 step per call, pinned host buffer)"}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         import oracle
         oracle.build()
         cores = oracle.set_threads(0)
-        P = oracle.Problem(**dict(sp.kwargs(), gamma=quench))
+        sp = gi.CONFIG_3D_TRAP
+        P = oracle.Problem(n=tuple(sp_n), lo=sp.lo, length=sp.length, g=sp.g, dt=sp.dt,
+                           gamma=tuple(2.0 * g for g in sp.gamma))
         x = psi.cpu().numpy().astype(np.complex128)
         n, t0 = 0, time.perf_counter()
         while True:
@@ -800,26 +906,17 @@ def run_trap(args):
             t = time.perf_counter() - t0
             if t > 20.0 or t * (n + 1) / n > 24.0:
                 break
-        cpu = {"value": sp.N * n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%d real-time step(s) of the quenched 256^3 trap on the FP64 oracle, %.1f s" % (n, t)}
+        cpu = {"value": N * n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d real-time step(s) of the quenched trap on the FP64 oracle, %.1f s" % (n, t)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_real / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "3D trap %s, gamma=(1,2,4) -> (2,4,8) after the ground state, g=200, "
-                                       "box [-8,8)^3, dt=1e-3, complex64 bulk / FP64 tables and reductions; "
-                                       "rms sizes read back every 10 real-time steps" % "x".join(map(str, sp.n)),
-                           "grid": list(sp.n), "l2": "state %.2f GiB > L2: no flush" % (state_bytes / 2 ** 30),
-                           "tiles_imag": tiles_i, "tiles_real": tiles_r},
-                "imag": {"c64": {"steps": int(done), "etol": 1e-6, "ms_per_step": ms_imag / max(1, done),
-                                 "updates_per_s": ws * sp.N * done / (ms_imag / 1e3), "E": float(e64[0])},
-                         "c128": {"steps": int(done128), "etol": 1e-10, "ms_per_step": ms_imag128 / max(1, done128),
-                                  "updates_per_s": ws * sp.N * done128 / (ms_imag128 / 1e3)},
-                         "converged": bool(done128 < args.imag_max), "E": float(e_ground[0]),
-                         "mu": float(ground[5]), "sigma": [float(v) for v in sig0[:3]], "r_rms": float(sig0[3])},
-                "sigma_final": [float(v) for v in sig[-1][:3]] if sig else None,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-                "gpu_launches": int(sum(c for c, _ in tr.values()))}
+                "config": {"workload": r["workload"], "grid": sp_n,
+                           "l2": "state %.2f GiB > L2: no flush" % (N * 8 / 2 ** 30),
+                           "tiles_imag": r["tiles_imag"], "tiles_real": r["tiles_real"]},
+                "imag": r["imag"], "sigma_final": r["sigma_final"], "roofline": r["roofline"],
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "gpu_launches": r["gpu_launches"]}
         print(json.dumps(line), flush=True)
     return 0
 
@@ -928,11 +1025,14 @@ def main():
     ap.add_argument("--imag-max", type=int, default=20000, help="trap256: imaginary-time step limit")
     ap.add_argument("--instances", type=int, default=512, help="batched: number of instances")
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
-    ap.add_argument("--max-active", type=int, default=32, help="serving: resident requests")
+    ap.add_argument("--max-active", type=int, default=0,
+                    help="serving: resident requests (0: derived from the 150 GB budget)")
     ap.add_argument("--max2d", type=int, default=2048, help="serving: largest 2D grid side")
     ap.add_argument("--max3d", type=int, default=256, help="serving: largest 3D grid side")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-sub", action="store_true", help="skip the batched and serving sub-records")
+    ap.add_argument("--tiles", default=None,
+                    help="fixed tile shapes x,y,z (0/1) instead of the autotuner, e.g. 0,1,1 (profiling runs)")
     ap.add_argument("--grid", default=None,
                     help="override the workload grid, e.g. 512,512,128 (profiling cases; same box and parameters)")
     args = ap.parse_args()

@@ -71,7 +71,14 @@ typedef struct gpe_result {
  * device memory (states plus group plans, estimated) fits in
  * hbm_budget_bytes; resident requests of the same group advance together in
  * chunks of at most chunk_steps steps (0: 64), and requests that finish leave
- * between chunks so that queued ones can enter. */
+ * between chunks so that queued ones can enter.  max_active <= 0 derives it
+ * from the budget: budget / 64 MiB, clamped to 16..256 (it also sizes every
+ * group plan: one parameter slot per resident request).
+ * Each scheduling round enqueues every group's work on its own stream before
+ * waiting for any: request states come from a server-owned stream-ordered
+ * memory pool (no device-wide synchronisation on admission or release), and
+ * imaginary-time sets copy their energies into pinned buffers that are read
+ * after the round's streams have been waited for. */
 gpe_status gpe_server_create(size_t hbm_budget_bytes, int max_active, int chunk_steps, gpe_server **out);
 gpe_status gpe_server_destroy(gpe_server *server);
 

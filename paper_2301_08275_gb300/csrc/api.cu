@@ -89,6 +89,7 @@ struct gpe_plan {
     void *vsamp = nullptr;       // sampled potential [N] in the bulk real type, or NULL
     double *g_dev = nullptr, *gamma_dev = nullptr, *scale = nullptr, *partials = nullptr;
     double *sums = nullptr, *out6 = nullptr, *out4 = nullptr;
+    double *ones = nullptr;                 // [batch] of 1.0 (resets the renormalisation factors)
     int *err = nullptr;
     int64_t lines_cap = 0;
     double *pin = nullptr;   // pinned host staging
@@ -125,6 +126,7 @@ struct gpe_plan {
     // trap tables of one time level (gpe_step_real_trap), allocated on first use
     void *sched[3] = {nullptr, nullptr, nullptr};
     void *sched_last = nullptr;
+    double *dtab = nullptr;                 // dither angles and offsets per step (resident kernel)
 };
 
 static gpe_status check_err(gpe_plan *p);
@@ -372,8 +374,16 @@ extern "C" gpe_status gpe_plan_create(const gpe_plan_desc *d, void *cuda_stream,
     PLAN_TRY(dalloc(p, (void **)&p->out6, sizeof(double) * 6 * B));
     PLAN_TRY(dalloc(p, (void **)&p->out4, sizeof(double) * 4 * B));
     PLAN_TRY(dalloc(p, (void **)&p->err, sizeof(int)));
+    PLAN_TRY(dalloc(p, (void **)&p->ones, sizeof(double) * B));
 #undef PLAN_TRY
     p->gamma_host = gam;
+    {
+        std::vector<double> one(B, 1.0);
+        if (cudaMemcpy(p->ones, one.data(), sizeof(double) * B, cudaMemcpyHostToDevice) != cudaSuccess) {
+            destroy(p);
+            return fail(GPE_ECUDA, "uploading plan parameters failed");
+        }
+    }
     if (cudaMemcpy(p->g_dev, gs.data(), sizeof(double) * B, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->gamma_dev, gam.data(), sizeof(double) * 3 * B, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess) {
@@ -707,8 +717,8 @@ static gpe_status check_psi(const gpe_plan *p, const void *psi)
 // sequence of the step index in the call, so results are reproducible.
 static double dither_angle(int64_t s)
 {
-    const double g = 0.6180339887498948482;      // golden-ratio sequence in [-0.01, 0.01)
-    const double f = (double)s * g + 0.5;
+    const double g = 0.6180339887498948482;      // golden-ratio sequence in [-0.01, 0.01), period 2^16
+    const double f = (double)(s & (GPE_DITHER_PERIOD - 1)) * g + 0.5;
     return 0.02 * (f - floor(f)) - 0.01;
 }
 static void set_dither(PassArgs &k, double phi)
@@ -1154,12 +1164,10 @@ extern "C" gpe_status gpe_rms_size(gpe_plan *p, const void *psi, double *out)
 }
 
 // ------------------------------------------------------------------ imaginary time
+// renormalisation factors back to one (a device-to-device copy: no host wait)
 static gpe_status fill_scale_one(gpe_plan *p)
 {
-    for (int64_t b = 0; b < p->batch && b < (int64_t)p->pin_len; ++b) p->pin[b] = 1.0;
-    // pin_len >= batch by construction
-    GPE_CUDA(cudaMemcpyAsync(p->scale, p->pin, sizeof(double) * p->batch, cudaMemcpyHostToDevice, p->st));
-    GPE_CUDA(cudaStreamSynchronize(p->st));
+    GPE_CUDA(cudaMemcpyAsync(p->scale, p->ones, sizeof(double) * p->batch, cudaMemcpyDeviceToDevice, p->st));
     return GPE_OK;
 }
 
@@ -1498,6 +1506,88 @@ gpe_status plan_run(gpe_plan *p, int mode, void *const *dptrs, const int *dslots
         s = diag_dev(p, psi);
         if (s == GPE_OK) s = copy_out(p, p->out6, 6 * (size_t)count, out6_host);
     }
+    p->cur_ptrs = nullptr;
+    p->cur_slots = nullptr;
+    p->cur_count = 0;
+    return s;
+}
+
+// Resident path for batches of small 2D complex64 instances: the dither
+// table (the values step_real_dev passes to its launches) once per plan, then
+// one launch that runs every step of the call on chip.
+bool plan_resident_ok(const gpe_plan *p) { return resident2d_supported(p->prec == GPE_C64 ? 0 : 1, p->ndim, p->n) && !p->vsamp; }
+
+gpe_status plan_prepare_resident(gpe_plan *p)
+{
+    if (p->dtab) return GPE_OK;
+    DeviceGuard dg(p->device);
+    std::vector<double> h(5 * (size_t)GPE_DITHER_PERIOD);
+    for (int64_t s = 0; s < GPE_DITHER_PERIOD; ++s) {
+        PassArgs k;
+        memset(&k, 0, sizeof(k));
+        const double phi = dither_angle(s);
+        set_dither(k, phi);
+        h[5 * s] = phi;
+        for (int q = 0; q < 4; ++q) h[5 * s + 1 + q] = k.dk[q];
+    }
+    GPE_TRY(dalloc(p, (void **)&p->dtab, sizeof(double) * h.size()));
+    GPE_CUDA(cudaMemcpy(p->dtab, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice));
+    return GPE_OK;
+}
+
+gpe_status plan_run_resident(gpe_plan *p, void *const *dptrs, const int *dslots, int64_t count, int64_t nsteps)
+{
+    if (!plan_resident_ok(p) || !p->dtab) return fail(GPE_EUNSUPPORTED, "resident path not prepared for this plan");
+    if (count < 1 || count > p->batch) return fail(GPE_EINVAL, "instance count out of range");
+    if (nsteps <= 0) return GPE_OK;
+    DeviceGuard dg(p->device);
+    ResidentArgs r;
+    memset(&r, 0, sizeof(r));
+    r.inst_ptr = dptrs;
+    r.slot_of = dslots;
+    r.count = count;
+    r.nsteps = nsteps;
+    r.tw = p->tw[0];
+    r.rows = make_pass(p, 0, nullptr, nullptr, count);
+    set_nreal(p, r.rows, true);
+    r.rows.op_mid = OP_NREAL;
+    r.cols = make_pass(p, 1, nullptr, nullptr, count);
+    r.cols.op_mid = OP_KREAL;
+    for (int a = 0; a < 2; ++a) {
+        r.vh[a] = p->vh[a];
+        r.vf[a] = p->vf[a];
+    }
+    r.dt = p->dt;
+    r.dither = p->prec == GPE_C64 && !p->no_dither;
+    r.dtab = p->dtab;
+    TraceScope ts(p, "resident2d" + std::to_string(p->n[0]) + ":real");
+    cudaError_t e = launch_resident2d((int)p->n[0], r, p->st);
+    if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("resident launch: ") + cudaGetErrorString(e));
+    return GPE_OK;
+}
+
+// The same without waiting: mode 1 enqueues nsteps imaginary-time steps and
+// then the diagnostics, mode 2 only the diagnostics; out6 (6*count doubles)
+// and the device error word are copied into the pinned host buffers out6_pin
+// and err_pin, and the error word is cleared.  The caller synchronises the
+// plan stream before it reads them.
+gpe_status plan_run_async(gpe_plan *p, int mode, void *const *dptrs, const int *dslots, int64_t count, int64_t nsteps,
+                          double target, double *out6_pin, int *err_pin)
+{
+    if (count < 1 || count > p->batch) return fail(GPE_EINVAL, "instance count out of range");
+    DeviceGuard dg(p->device);
+    p->cur_ptrs = dptrs;
+    p->cur_slots = dslots;
+    p->cur_count = count;
+    gpe_status s = GPE_OK;
+    void *psi = const_cast<void *>(static_cast<const void *>(dptrs));
+    if (mode == 1) s = imag_steps(p, psi, nsteps, target);
+    if (s == GPE_OK) s = diag_dev(p, psi);
+    if (s == GPE_OK &&
+        (cudaMemcpyAsync(out6_pin, p->out6, sizeof(double) * 6 * count, cudaMemcpyDeviceToHost, p->st) != cudaSuccess ||
+         cudaMemcpyAsync(err_pin, p->err, sizeof(int), cudaMemcpyDeviceToHost, p->st) != cudaSuccess ||
+         cudaMemsetAsync(p->err, 0, sizeof(int), p->st) != cudaSuccess))
+        s = fail(GPE_ECUDA, "copying results back failed");
     p->cur_ptrs = nullptr;
     p->cur_slots = nullptr;
     p->cur_count = 0;

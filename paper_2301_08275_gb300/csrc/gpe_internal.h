@@ -103,6 +103,23 @@ cudaError_t launch_pass(int prec, bool rows, const PassArgs &a, cudaStream_t st,
 int pass_lines_per_tile(int prec, bool rows, int n, int var = 0);
 
 // whole 1D steps with each line (instance) resident on chip for all steps
+// Real-time stepping of small 2D complex64 instances held in shared memory
+// for a whole call (resident.cu).
+#define GPE_DITHER_PERIOD 65536   // the phase dither sequence repeats after this many steps
+struct ResidentArgs {
+    void *const *inst_ptr;     // instance b at inst_ptr[b] (n x n points, x fastest)
+    const int *slot_of;        // its parameter/table slot, or NULL (slot b)
+    int64_t count, nsteps;
+    const void *tw;            // natural twiddle table of the n-point lines
+    PassArgs rows, cols;       // argument templates of the row (nonlinear) and column (kinetic) sweeps
+    const void *vh[2], *vf[2]; // trap tables of x and y (half and full steps), or NULL
+    double dt;
+    int dither;                // 1: the complex64 phase dither of the real-time step
+    const double *dtab;        // [GPE_DITHER_PERIOD][5]: phi, then the offset of exp(-i phi) as hi, hi, lo, lo
+};
+cudaError_t launch_resident2d(int n, const ResidentArgs &a, cudaStream_t st);
+bool resident2d_supported(int prec, int ndim, const int64_t *n);
+
 struct Line1DArgs {
     void *psi;
     int64_t batch;

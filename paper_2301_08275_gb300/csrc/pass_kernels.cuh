@@ -72,20 +72,19 @@ __device__ __forceinline__ float2 phase_offset(float th)
 }
 
 // v_e <- v_e (1 + w_e), w_e = exp(-i th_e) - 1, for the E angles a thread
-// holds: the short series when every angle of the warp is at most 1/16 (the
-// usual case: dt |V + g|psi|^2| is far below it), else the long form
+// holds: the short series for every angle of at most 1/16 (the usual case:
+// dt |V + g|psi|^2| is far below it), the long form for the others.  The
+// choice is made per element, so a point's result does not depend on which
+// lines share its warp (tile shapes and kernels with other thread layouts
+// give the same bits); a warp whose angles are all small takes one branch.
 template <typename C, typename R, int E>
 __device__ __forceinline__ void apply_phase(C (&v)[E], const R (&th)[E])
 {
-    R mx = (R)0;
 #pragma unroll
-    for (int e = 0; e < E; ++e) mx = fmax(mx, fabs(th[e]));
-    if (__all_sync(__activemask(), mx <= (R)0.0625)) {
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = cmadd1(v[e], phase_offset_small(th[e]));
-    } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = cmadd1(v[e], phase_offset(th[e]));
+    for (int e = 0; e < E; ++e) {
+        auto w = phase_offset_small(th[e]);
+        if (fabs(th[e]) > (R)0.0625) w = phase_offset(th[e]);
+        v[e] = cmadd1(v[e], w);
     }
 }
 

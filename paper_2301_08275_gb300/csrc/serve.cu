@@ -37,6 +37,11 @@ gpe_status plan_set_slot(gpe_plan *p, int64_t slot, double g, const double *gamm
 gpe_status plan_prepare(gpe_plan *p);
 gpe_status plan_run(gpe_plan *p, int mode, void *const *dptrs, const int *dslots, int64_t count, int64_t nsteps,
                     double target, double *out6_host);
+gpe_status plan_run_async(gpe_plan *p, int mode, void *const *dptrs, const int *dslots, int64_t count, int64_t nsteps,
+                          double target, double *out6_pin, int *err_pin);
+bool plan_resident_ok(const gpe_plan *p);
+gpe_status plan_prepare_resident(gpe_plan *p);
+gpe_status plan_run_resident(gpe_plan *p, void *const *dptrs, const int *dslots, int64_t count, int64_t nsteps);
 }  // namespace gpe
 
 using namespace gpe;
@@ -94,6 +99,7 @@ struct BGroup {
     gpe_plan *plan = nullptr;
     cudaStream_t st = nullptr;
     cudaEvent_t done = nullptr;
+    bool resident = false;         // small 2D complex64 instances: stepped on chip (resident.cu)
     std::vector<int> members;      // instance indices of the batch
     void **d_ptrs = nullptr;
     int *d_slots = nullptr;
@@ -174,7 +180,11 @@ extern "C" gpe_status gpe_batch_create(const gpe_plan_desc *descs, int count, vo
         if (s == GPE_OK) s = gpe_plan_create(&d, g.st, &g.plan);
         // tile shapes timed on this group's grid (per-thread staging: the group's
         // instances are reached through a pointer array)
-        if (s == GPE_OK) s = gpe_plan_autotune(g.plan, nullptr, 3, GPE_TUNE_NO_TMA);
+        if (s == GPE_OK) {
+            g.resident = plan_resident_ok(g.plan);
+            if (g.resident) s = plan_prepare_resident(g.plan);
+            else s = gpe_plan_autotune(g.plan, nullptr, 3, GPE_TUNE_NO_TMA);
+        }
         if (s == GPE_OK) s = plan_prepare(g.plan);
         if (s == GPE_OK && (cudaMalloc((void **)&g.d_ptrs, sizeof(void *) * n) != cudaSuccess ||
                             cudaMalloc((void **)&g.d_slots, sizeof(int) * n) != cudaSuccess))
@@ -225,7 +235,9 @@ static gpe_status batch_enqueue(gpe_batch *b, cudaStream_t root, int64_t nsteps)
     S_CUDA(cudaEventRecord(b->fork, root));
     for (auto &g : b->groups) {
         S_CUDA(cudaStreamWaitEvent(g.st, b->fork, 0));
-        gpe_status s = plan_run(g.plan, 0, g.d_ptrs, g.d_slots, (int64_t)g.members.size(), nsteps, 1.0, nullptr);
+        gpe_status s = g.resident
+                           ? plan_run_resident(g.plan, g.d_ptrs, g.d_slots, (int64_t)g.members.size(), nsteps)
+                           : plan_run(g.plan, 0, g.d_ptrs, g.d_slots, (int64_t)g.members.size(), nsteps, 1.0, nullptr);
         if (s != GPE_OK) return s;
         S_CUDA(cudaEventRecord(g.done, g.st));
         S_CUDA(cudaStreamWaitEvent(root, g.done, 0));
@@ -307,6 +319,11 @@ struct SGroup {
     void **d_ptrs = nullptr;
     int *d_slots = nullptr;
     size_t bytes = 0;
+    // pinned landing buffers of the energies and error words of one round's
+    // launch sets (at most one set per member, plus the first-energy set)
+    double *pin_out = nullptr;   // [6 * (2 cap + 1)]: every member at most twice per round
+    int *pin_err = nullptr;      // [cap + 2]: one word per launch set
+    int cap = 0;
 };
 
 }  // namespace
@@ -315,6 +332,7 @@ struct gpe_server {
     size_t budget = 0, used = 0;
     int max_active = 0, chunk = 64;
     int device = 0;
+    cudaMemPool_t pool = nullptr;   // stream-ordered allocations of the request states
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Req *> queue;
@@ -344,11 +362,15 @@ static size_t group_bytes(const gpe_plan_desc &d, int cap)
 
 static gpe_status finish_req(gpe_server *s, SGroup *g, Req *r, gpe_status st)
 {
-    // result back to the host copy, device state released
+    // result back to the host copy (its stream is idle here: the round has
+    // synchronised it), device state returned to the pool without a device-wide wait
     if (r->dpsi) {
-        if (st == GPE_OK && cudaMemcpy(r->psi_host.data(), r->dpsi, r->psi_host.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        cudaStream_t rs = g ? g->st : nullptr;
+        if (st == GPE_OK && (cudaMemcpyAsync(r->psi_host.data(), r->dpsi, r->psi_host.size(), cudaMemcpyDeviceToHost,
+                                             rs) != cudaSuccess ||
+                             cudaStreamSynchronize(rs) != cudaSuccess))
             st = GPE_ECUDA;
-        cudaFree(r->dpsi);
+        cudaFreeAsync(r->dpsi, rs);
         r->dpsi = nullptr;
     }
     if (g && r->slot >= 0) g->free_slots.push_back(r->slot);
@@ -409,12 +431,19 @@ static void admit(gpe_server *s)
             if (st == GPE_OK && (cudaMalloc((void **)&g->d_ptrs, sizeof(void *) * d.batch) != cudaSuccess ||
                                  cudaMalloc((void **)&g->d_slots, sizeof(int) * d.batch) != cudaSuccess))
                 st = GPE_ENOMEM;
+            g->cap = d.batch;
+            if (st == GPE_OK &&
+                (cudaMallocHost((void **)&g->pin_out, sizeof(double) * 6 * (size_t)(2 * d.batch + 1)) != cudaSuccess ||
+                 cudaMallocHost((void **)&g->pin_err, sizeof(int) * (size_t)(d.batch + 2)) != cudaSuccess))
+                st = GPE_ENOMEM;
             for (int j = d.batch - 1; j >= 0; --j) g->free_slots.push_back(j);
             if (st != GPE_OK) {
                 if (g->plan) gpe_plan_destroy(g->plan);
                 if (g->st) cudaStreamDestroy(g->st);
                 if (g->d_ptrs) cudaFree(g->d_ptrs);
                 if (g->d_slots) cudaFree(g->d_slots);
+                if (g->pin_out) cudaFreeHost(g->pin_out);
+                if (g->pin_err) cudaFreeHost(g->pin_err);
                 delete g;
                 g = nullptr;
                 std::lock_guard<std::mutex> lk(s->mu);
@@ -424,8 +453,15 @@ static void admit(gpe_server *s)
                 s->groups[r->key] = g;
             }
         }
-        if (st == GPE_OK && cudaMalloc(&r->dpsi, r->psi_host.size()) != cudaSuccess) st = GPE_ENOMEM;
-        if (st == GPE_OK && cudaMemcpy(r->dpsi, r->psi_host.data(), r->psi_host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        // state from the server's pool, ordered on the group stream: neither the
+        // allocation nor the upload waits for the device (the pageable source
+        // is staged by the driver before the call returns)
+        if (st == GPE_OK && cudaMallocFromPoolAsync(&r->dpsi, r->psi_host.size(), s->pool, g->st) != cudaSuccess) {
+            r->dpsi = nullptr;
+            st = GPE_ENOMEM;
+        }
+        if (st == GPE_OK &&
+            cudaMemcpyAsync(r->dpsi, r->psi_host.data(), r->psi_host.size(), cudaMemcpyHostToDevice, g->st) != cudaSuccess)
             st = GPE_ECUDA;
         if (st == GPE_OK) {
             r->slot = g->free_slots.back();
@@ -451,17 +487,20 @@ static bool upload_members(SGroup *g, const std::vector<Req *> &ms)
         hp[j] = ms[j]->dpsi;
         hs[j] = ms[j]->slot;
     }
+    // pageable sources: staged by the driver before each call returns, so the
+    // vectors may go out of scope; the copies stay ordered on the group stream
     return cudaMemcpyAsync(g->d_ptrs, hp.data(), sizeof(void *) * hp.size(), cudaMemcpyHostToDevice, g->st) == cudaSuccess &&
-           cudaMemcpyAsync(g->d_slots, hs.data(), sizeof(int) * hs.size(), cudaMemcpyHostToDevice, g->st) == cudaSuccess &&
-           cudaStreamSynchronize(g->st) == cudaSuccess;
+           cudaMemcpyAsync(g->d_slots, hs.data(), sizeof(int) * hs.size(), cudaMemcpyHostToDevice, g->st) == cudaSuccess;
 }
 
-// One scheduling round.  Real-time groups advance all members by one chunk
-// (the smallest remaining step count, capped) in one launch sequence, all
-// groups enqueued before any is waited for; chunking is exact there.  In
-// imaginary time each member advances exactly min(check_every, remaining)
-// steps between energy checks, as gpe_step_imag does, so members are launched
-// in sets of equal chunk.
+// One scheduling round, in two phases.  First every group's work is
+// enqueued on its own stream without waiting: real-time groups advance all
+// members by one chunk (the smallest remaining step count, capped; chunking
+// is exact); imaginary-time groups take the energy of new members' inputs,
+// then advance sets of members with equal chunk, exactly min(check_every,
+// remaining) steps between energy checks as gpe_step_imag does, each set's
+// energies and error word copied into pinned buffers.  Then each stream is
+// waited for once and the sets are retired in the order they were enqueued.
 static void round_once(gpe_server *s)
 {
     std::vector<SGroup *> gs;
@@ -470,13 +509,98 @@ static void round_once(gpe_server *s)
         for (auto &kv : s->groups)
             if (!kv.second->members.empty()) gs.push_back(kv.second);
     }
-    auto retire = [&](SGroup *g, const std::vector<Req *> &ms, int64_t chunk, gpe_status st, const double *o6) {
-        for (size_t j = 0; j < ms.size(); ++j) {
-            Req *r = ms[j];
-            r->done_steps += chunk;
-            if (o6) {
-                r->res.norm = o6[6 * j + 0];
-                r->res.energy = o6[6 * j + 4];
+    struct Pending {
+        SGroup *g;
+        std::vector<Req *> ms;
+        int64_t chunk;
+        int kind;            // 0 real-time chunk, 1 imaginary-time set, 2 first energies
+        double *o6;          // pinned energies, or NULL
+        int *err;            // pinned error word, or NULL
+        gpe_status st;       // enqueue status
+    };
+    std::vector<Pending> pend;
+    for (SGroup *g : gs) {
+        int used_sets = 0;
+        size_t used_out = 0;
+        auto land = [&](size_t count, double **o6, int **err) {
+            *o6 = g->pin_out + 6 * used_out;
+            used_out += count;
+            *err = g->pin_err + used_sets;
+            ++used_sets;
+        };
+        if (!g->imag) {
+            int64_t chunk = s->chunk;
+            for (Req *r : g->members) chunk = std::min(chunk, r->r.nsteps - r->done_steps);
+            chunk = std::max<int64_t>(chunk, 1);
+            gpe_status st = upload_members(g, g->members) ? GPE_OK : GPE_ECUDA;
+            if (st == GPE_OK)
+                st = plan_run(g->plan, 0, g->d_ptrs, g->d_slots, (int64_t)g->members.size(), chunk, 1.0, nullptr);
+            // energies only when someone finishes (the report of the final state)
+            bool need = false;
+            for (Req *r : g->members) need = need || r->done_steps + chunk >= r->r.nsteps;
+            double *o6 = nullptr;
+            int *err = nullptr;
+            if (st == GPE_OK && need) {
+                land(g->members.size(), &o6, &err);
+                st = plan_run_async(g->plan, 2, g->d_ptrs, g->d_slots, (int64_t)g->members.size(), 0, 1.0, o6, err);
+            }
+            pend.push_back({g, g->members, chunk, 0, o6, err, st});
+            continue;
+        }
+        std::vector<Req *> fresh;
+        for (Req *r : g->members)
+            if (!r->has_e0) fresh.push_back(r);
+        if (!fresh.empty()) {
+            double *o6;
+            int *err;
+            land(fresh.size(), &o6, &err);
+            gpe_status st = upload_members(g, fresh) ? GPE_OK : GPE_ECUDA;
+            if (st == GPE_OK)
+                st = plan_run_async(g->plan, 2, g->d_ptrs, g->d_slots, (int64_t)fresh.size(), 0, 1.0, o6, err);
+            pend.push_back({g, fresh, 0, 2, o6, err, st});
+        }
+        std::map<int64_t, std::vector<Req *>> sets;
+        for (Req *r : g->members)
+            sets[std::min<int64_t>(r->r.check_every, r->r.nsteps - r->done_steps)].push_back(r);
+        for (auto &kv : sets) {
+            const int64_t chunk = std::max<int64_t>(kv.first, 1);
+            double *o6;
+            int *err;
+            land(kv.second.size(), &o6, &err);
+            gpe_status st = upload_members(g, kv.second) ? GPE_OK : GPE_ECUDA;
+            if (st == GPE_OK)
+                st = plan_run_async(g->plan, 1, g->d_ptrs, g->d_slots, (int64_t)kv.second.size(), chunk,
+                                    kv.second[0]->r.target_norm, o6, err);
+            pend.push_back({g, kv.second, chunk, 1, o6, err, st});
+        }
+    }
+    std::map<SGroup *, gpe_status> synced;
+    for (SGroup *g : gs) synced[g] = cudaStreamSynchronize(g->st) == cudaSuccess ? GPE_OK : GPE_ECUDA;
+    for (Pending &pd : pend) {
+        SGroup *g = pd.g;
+        gpe_status st = pd.st != GPE_OK ? pd.st : synced[g];
+        if (st == GPE_OK && pd.err && *pd.err)
+            st = (*pd.err & ERR_TMA_TIMEOUT) ? GPE_ETIMEOUT : GPE_ENUMERIC;
+        if (pd.kind == 2) {
+            for (size_t j = 0; j < pd.ms.size(); ++j) {
+                Req *r = pd.ms[j];
+                if (st != GPE_OK) {
+                    finish_req(s, g, r, st);
+                    g->members.erase(std::find(g->members.begin(), g->members.end(), r));
+                    continue;
+                }
+                r->e_prev = pd.o6[6 * j + 4];
+                r->has_e0 = true;
+            }
+            continue;
+        }
+        for (size_t j = 0; j < pd.ms.size(); ++j) {
+            Req *r = pd.ms[j];
+            if (std::find(g->members.begin(), g->members.end(), r) == g->members.end()) continue;   // retired earlier
+            if (st == GPE_OK) r->done_steps += pd.chunk;
+            if (pd.o6 && st == GPE_OK) {
+                r->res.norm = pd.o6[6 * j + 0];
+                r->res.energy = pd.o6[6 * j + 4];
             }
             bool finished = st != GPE_OK || r->done_steps >= r->r.nsteps;
             gpe_status rs = st;
@@ -494,65 +618,6 @@ static void round_once(gpe_server *s)
                 g->members.erase(std::find(g->members.begin(), g->members.end(), r));
             }
         }
-    };
-    std::vector<std::pair<SGroup *, int64_t>> real_launched;
-    for (SGroup *g : gs) {
-        if (!g->imag) {
-            int64_t chunk = s->chunk;
-            for (Req *r : g->members) chunk = std::min(chunk, r->r.nsteps - r->done_steps);
-            chunk = std::max<int64_t>(chunk, 1);
-            gpe_status st = upload_members(g, g->members) ? GPE_OK : GPE_ECUDA;
-            if (st == GPE_OK)
-                st = plan_run(g->plan, 0, g->d_ptrs, g->d_slots, (int64_t)g->members.size(), chunk, 1.0, nullptr);
-            if (st != GPE_OK) {
-                std::vector<Req *> ms = g->members;
-                retire(g, ms, 0, st, nullptr);
-                continue;
-            }
-            real_launched.push_back({g, chunk});
-            continue;
-        }
-        // imaginary time: initial energies of new members, then sets of equal chunk
-        std::vector<Req *> fresh;
-        for (Req *r : g->members)
-            if (!r->has_e0) fresh.push_back(r);
-        if (!fresh.empty()) {
-            std::vector<double> o6(6 * fresh.size());
-            gpe_status st = upload_members(g, fresh) ? GPE_OK : GPE_ECUDA;
-            if (st == GPE_OK) st = plan_run(g->plan, 2, g->d_ptrs, g->d_slots, (int64_t)fresh.size(), 0, 1.0, o6.data());
-            if (st != GPE_OK) {
-                retire(g, fresh, 0, st, nullptr);
-                continue;
-            }
-            for (size_t j = 0; j < fresh.size(); ++j) {
-                fresh[j]->e_prev = o6[6 * j + 4];
-                fresh[j]->has_e0 = true;
-            }
-        }
-        std::map<int64_t, std::vector<Req *>> sets;
-        for (Req *r : g->members)
-            sets[std::min<int64_t>(r->r.check_every, r->r.nsteps - r->done_steps)].push_back(r);
-        for (auto &kv : sets) {
-            const int64_t chunk = std::max<int64_t>(kv.first, 1);
-            std::vector<Req *> &ms = kv.second;
-            std::vector<double> o6(6 * ms.size());
-            gpe_status st = upload_members(g, ms) ? GPE_OK : GPE_ECUDA;
-            if (st == GPE_OK)
-                st = plan_run(g->plan, 1, g->d_ptrs, g->d_slots, (int64_t)ms.size(), chunk, ms[0]->r.target_norm, nullptr);
-            if (st == GPE_OK) st = plan_run(g->plan, 2, g->d_ptrs, g->d_slots, (int64_t)ms.size(), 0, 1.0, o6.data());
-            retire(g, ms, chunk, st, st == GPE_OK ? o6.data() : nullptr);
-        }
-    }
-    for (auto &gc : real_launched) {
-        SGroup *g = gc.first;
-        std::vector<Req *> ms = g->members;
-        gpe_status st = cudaStreamSynchronize(g->st) == cudaSuccess ? GPE_OK : GPE_ECUDA;
-        // energies only when someone finishes (the report of the final state)
-        bool need = false;
-        for (Req *r : ms) need = need || r->done_steps + gc.second >= r->r.nsteps;
-        std::vector<double> o6(6 * ms.size(), 0.0);
-        if (st == GPE_OK && need) st = plan_run(g->plan, 2, g->d_ptrs, g->d_slots, (int64_t)ms.size(), 0, 1.0, o6.data());
-        retire(g, ms, gc.second, st, need && st == GPE_OK ? o6.data() : nullptr);
     }
 }
 
@@ -573,15 +638,29 @@ static void worker_main(gpe_server *s)
 
 extern "C" gpe_status gpe_server_create(size_t hbm_budget_bytes, int max_active, int chunk_steps, gpe_server **out)
 {
-    if (!out || max_active < 1 || hbm_budget_bytes == 0) return sfail(GPE_EINVAL, "gpe_server_create: bad arguments");
+    if (!out || hbm_budget_bytes == 0) return sfail(GPE_EINVAL, "gpe_server_create: bad arguments");
     gpe_server *s = new gpe_server();
     s->budget = hbm_budget_bytes;
-    s->max_active = max_active;
+    // max_active <= 0: as many resident requests as the budget holds at 64 MiB
+    // each (a 256^3 complex64 state is 128 MiB, a 1024^2 one 8 MiB), 16..256
+    s->max_active = max_active > 0 ? max_active
+                                   : (int)std::max<size_t>(16, std::min<size_t>(256, hbm_budget_bytes / (64ull << 20)));
     s->chunk = chunk_steps > 0 ? chunk_steps : 64;
     if (cudaGetDevice(&s->device) != cudaSuccess) {
         delete s;
         return sfail(GPE_ECUDA, "cudaGetDevice failed");
     }
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = s->device;
+    if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) {
+        delete s;
+        return sfail(GPE_ECUDA, "cudaMemPoolCreate failed");
+    }
+    // keep freed states in the pool up to the budget instead of returning them
+    cuuint64_t keep = (cuuint64_t)hbm_budget_bytes;
+    cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     s->worker = std::thread(worker_main, s);
     *out = s;
     return GPE_OK;
@@ -596,6 +675,7 @@ extern "C" gpe_status gpe_server_destroy(gpe_server *s)
     }
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
+    cudaDeviceSynchronize();
     for (auto &kv : s->reqs) {
         if (kv.second->dpsi) cudaFree(kv.second->dpsi);
         delete kv.second;
@@ -606,8 +686,11 @@ extern "C" gpe_status gpe_server_destroy(gpe_server *s)
         if (g->st) cudaStreamDestroy(g->st);
         if (g->d_ptrs) cudaFree(g->d_ptrs);
         if (g->d_slots) cudaFree(g->d_slots);
+        if (g->pin_out) cudaFreeHost(g->pin_out);
+        if (g->pin_err) cudaFreeHost(g->pin_err);
         delete g;
     }
+    if (s->pool) cudaMemPoolDestroy(s->pool);
     delete s;
     return GPE_OK;
 }

@@ -75,6 +75,30 @@ def test_batch_equals_individual_plans_and_oracle(gpe, orc, prec, use_graph):
     gpe.gpe_batch_destroy(b)
 
 
+def test_resident_batch_groups_equal_individual_plans(gpe):
+    """64^2 and 128^2 complex64 groups are stepped in shared memory for the
+    whole call (one launch per group); they give the bits of per-instance
+    plans, including instances with g up to 1000 whose nonlinear angles exceed
+    1/16 in the core (the long series there)."""
+    import torch
+    items = [(sp, psi) for sp, psi in gi.batched_specs(count=24, seed=7, sizes=(64, 128))]
+    xs = [torch.from_numpy(psi.astype(np.complex64)).cuda() for _, psi in items]
+    ys = [x.clone() for x in xs]
+    stream = torch.cuda.current_stream()
+    b = gpe.gpe_batch_create([desc_of(gpe, sp, gpe.GPE_C64) for sp, _ in items], stream.cuda_stream)
+    steps = 40
+    gpe.gpe_batch_step_real(b, [x.data_ptr() for x in xs], steps, True)
+    torch.cuda.synchronize()
+    assert max(sp.g for sp, _ in items) > 500
+    for (sp, _), x, y in zip(items, xs, ys):
+        p = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma, prec=gpe.GPE_C64)
+        p.step_real(y, steps)
+        torch.cuda.synchronize()
+        assert torch.equal(x, y)
+        p.close()
+    gpe.gpe_batch_destroy(b)
+
+
 def _standalone(gpe, sp, psi0, prec, imag, nsteps, etol=0.0, check_every=1):
     import torch
     p = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma[: sp.ndim], prec=prec)
