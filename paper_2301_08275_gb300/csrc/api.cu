@@ -585,6 +585,12 @@ static PassArgs make_pass(const gpe_plan *p, int axis, const void *src, void *ds
     a.vsamp_diag = p->vsamp;
     a.g = p->g_dev;
     a.inv_n = 1.0 / (double)p->N;
+    // states of up to 64 MiB (1024^2 complex64 is 8 MiB): every sweep is one
+    // short wave of CTAs, and the next kernel's launch may start with it
+    // (1024^2 complex64 step 27.1 -> 25.5 us); larger states trigger it at
+    // the end of each CTA (512^3 complex64: 2.39 ms/step with the early
+    // trigger, 2.15 with the late one, 2.16 without dependent launch)
+    a.pdl_early = (double)p->N * (double)batch * (p->prec == GPE_C64 ? 8.0 : 16.0) <= 64.0 * 1048576.0;
     a.scale = p->scale;
     a.partials = p->partials;
     a.lines_cap = p->lines_cap;

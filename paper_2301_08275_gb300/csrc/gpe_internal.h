@@ -66,6 +66,12 @@ struct PassArgs {
     double dk[4];
     double dphi;
     double inv_n;          // 1/N applied with the kinetic substep
+    // programmatic dependent launch: 1 lets the next kernel of the stream
+    // start its launch as soon as every CTA of this one has begun (grids that
+    // are resident at once: small states), 0 once every CTA has written its
+    // tiles (so that waiting CTAs of the next kernel do not hold SM resources
+    // while this one still has tiles to run)
+    int pdl_early;
     const double *scale;   // per-instance renormalisation factor
     // optional indirection for batches of separately allocated instances:
     // instance b lives at inst_ptr[b] (src = dst = that pointer) and takes its

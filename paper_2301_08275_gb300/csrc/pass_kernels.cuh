@@ -578,6 +578,13 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
         __syncthreads();
     }
     int issued[2] = {0, 0};   // boxes sets issued into each buffer (thread 0)
+    // Programmatic dependent launch: everything above (twiddles, barriers)
+    // touches nothing the previous kernel of the stream writes, so it may
+    // overlap that kernel's tail; the state is read only after this wait,
+    // which returns once the previous grid has completed and its writes are
+    // visible.  Without the launch attribute it returns at once.
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    if (a.pdl_early) asm volatile("griddepcontrol.launch_dependents;\n" :::);
 
     auto stage = [&](int64_t tile, C *buf, int b) {
         if (tma) {
@@ -758,6 +765,9 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
         __syncthreads();         // every thread is done with this buffer
         stage(tile + 2 * (int64_t)gridDim.x, sm, it & 1);
     }
+    // this CTA's tiles are written: the next kernel may start its launch (its
+    // CTAs still wait for this whole grid before they read the state)
+    asm volatile("griddepcontrol.launch_dependents;\n" :::);
     if (!tma) {
         cp_async_wait<0>();
     } else if (aborted && t == 0) {
@@ -929,8 +939,19 @@ static cudaError_t launch_pass_p(const PassArgs &a, cudaStream_t st, const CUten
     if (e != cudaSuccess) return e;
     if (a.ntiles <= 0) return cudaSuccess;
     const int grid = (int)(a.ntiles < cap ? a.ntiles : cap);
-    k_pass<R, N, ROWS, VAR, PROG><<<grid, T::NT, smem, st>>>(a, tmap ? *tmap : none);
-    return cudaGetLastError();
+    // launched with programmatic stream serialisation: the kernel waits for
+    // its predecessor in the stream itself (griddepcontrol.wait)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(T::NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_pass<R, N, ROWS, VAR, PROG>, a, tmap ? *tmap : none);
 }
 
 // complex64 lines of 256 to 1024 points (the large grids) get the fixed-program
