@@ -210,11 +210,24 @@ def alu_roofline(gpe, stream, kind, avg_ms, npoints, kernels):
     peak = gpe.gpe_measure_fp64_peak(stream.cuda_stream) / 1e12
     flops = pass_flops_per_point(kind) * npoints
     achieved = flops / (avg_ms / 1e3) / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": kind, "kernel_avg_ms": avg_ms, "flops_per_launch": flops,
-            "peak_source": "measured: gpe_measure_fp64_peak (independent FP64 FMA chains on every SM)",
-            "flops_model": "5 log2(n) per n-point transform + 6 per pointwise complex multiply, per point",
-            "kernels": kernels}
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": None, "kernel": kind, "kernel_avg_ms": avg_ms, "flops_per_launch": flops,
+           "peak_source": "measured: gpe_measure_fp64_peak (independent FP64 FMA chains on every SM)",
+           "flops_model": "5 log2(n) per n-point transform + 6 per pointwise complex multiply, per point",
+           "kernels": kernels}
+    if kind == "line1d256:real":
+        # one 256-point line is a latency problem, not a throughput one: its
+        # cluster of 16 CTAs (one warp each) issues one FP64 warp instruction
+        # per 64 cycles per SM sub-partition (measured), and a step is 62 such
+        # instructions in a chain plus two all-to-all exchanges (0.31 us each,
+        # measured for 16 CTAs)
+        steps = npoints / 256
+        model_us = 62 * 64 / 2.07e3 + 2 * 0.31
+        out["latency_model"] = {"us_per_step_model": model_us, "us_per_step": 1e3 * avg_ms / steps,
+                                "frac": model_us / (1e3 * avg_ms / steps),
+                                "model": "62 dependent FP64 warp instructions x 64 cycles at 2.07 GHz + two "
+                                         "cluster exchanges of 0.31 us (one line over a cluster of 16 CTAs)"}
+    return out
 
 
 def gpu_parity(plan, key, spec, prec, ref, nsteps):
@@ -380,7 +393,7 @@ def config_record(key, steps=None):
     state_bytes = spec.N * (8 if prec == gpe.GPE_C64 else 16)
     if prec == gpe.GPE_C128:
         # a 1D launch runs every step of the call: its flops per launch scale with them
-        per_launch = spec.N * (min(steps, 200) if kind.startswith("line1d") else 1)
+        per_launch = spec.N * (min(steps, 200) / cnt if kind.startswith("line1d") else 1)
         roof = alu_roofline(gpe, stream, kind, tot / cnt, per_launch, kernels)
     else:
         peak, src = measured_peaks()
@@ -468,7 +481,9 @@ def run_ours(args, key, wl):
                for k, (c, t) in tr.items()}
     state_bytes = spec.N * (8 if prec == gpe.GPE_C64 else 16)
     if prec == gpe.GPE_C128:
-        roofline = alu_roofline(gpe, stream, kind, avg_ms, spec.N, kernels)
+        # a 1D launch runs every step of its call: its flops per launch scale with them
+        per_launch = spec.N * (args.steps / cnt if kind.startswith("line1d") else 1)
+        roofline = alu_roofline(gpe, stream, kind, avg_ms, per_launch, kernels)
     else:
         peak, peak_src = measured_peaks()
         achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9

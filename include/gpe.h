@@ -192,6 +192,14 @@ gpe_status gpe_spectrum(gpe_plan *plan, const void *psi_dev, unsigned kinds, dou
  *                        errors of slowly turning modes from adding up
  *                        coherently (norm drift).  Unlike the options above
  *                        it changes the bits of complex64 results.
+ *   GPE_OPT_LINE_CLUSTER 1 (default): complex128 real-time steps of 1D
+ *                        plans with lines of 64, 128 or 256 points and at
+ *                        most 32 instances spread each line over a cluster
+ *                        of 4, 8 or 16 CTAs (a latency path: FP64 work on
+ *                        one SM is slow on this GPU); 0: one CTA per line.
+ *                        The two factor the transform differently, so their
+ *                        results differ in rounding (both agree with the
+ *                        FP64 reference to about 1e-14 per step).
  *   GPE_OPT_TEST_STALL_COPIES  test hook for the failure handling: 1 makes
  *                        every copy-engine tile wait expect 16 bytes more than
  *                        its copies deliver, so the wait runs out after its
@@ -209,6 +217,7 @@ enum gpe_option {
     GPE_OPT_TMA_Z = 6,
     GPE_OPT_GENERIC_PASSES = 7,
     GPE_OPT_NO_DITHER = 8,
+    GPE_OPT_LINE_CLUSTER = 9,
     GPE_OPT_TEST_STALL_COPIES = 99
 };
 gpe_status gpe_plan_set_option(gpe_plan *plan, int option, int64_t value);

@@ -226,6 +226,7 @@ def gpe_norm_energy_noalloc(desc, psi_ptr, stream=None):
 GPE_OPT_TMA_STAGING, GPE_OPT_TILE_X, GPE_OPT_TILE_Y, GPE_OPT_TILE_Z, GPE_OPT_TMA_Y, GPE_OPT_TMA_Z = 1, 2, 3, 4, 5, 6
 GPE_OPT_GENERIC_PASSES = 7
 GPE_OPT_NO_DITHER = 8
+GPE_OPT_LINE_CLUSTER = 9
 GPE_OPT_TEST_STALL_COPIES = 99
 GPE_TUNE_NO_TMA = 1
 

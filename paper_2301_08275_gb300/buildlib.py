@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libgpe.so")
 SOURCES = ["pass_f32_w512_0.cu", "pass_f32_w512_1.cu", "pass_f32_w1024_0.cu", "pass_f32_w1024_1.cu",
            "pass_f32_w256_0.cu", "pass_f32_w256_1.cu", "pass_f32.cu", "pass_f32_s1.cu", "pass_f32_rows.cu",
            "pass_f32_rows1.cu", "pass_f64.cu", "pass_f64_s1.cu", "pass_f64_rows.cu", "pass_f64_rows1.cu",
-           "diag_spec.cu", "api.cu", "noalloc.cu", "serve.cu", "peak.cu", "resident.cu"]
+           "diag_spec.cu", "api.cu", "noalloc.cu", "serve.cu", "peak.cu", "resident.cu", "line_cluster.cu"]
 HEADERS = ["fft_tile.cuh", "pass_kernels.cuh", "gpe_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]

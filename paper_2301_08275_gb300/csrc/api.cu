@@ -39,6 +39,11 @@ int pass_lines_per_tile(int prec, bool rows, int n, int var)
 }
 cudaError_t launch_line1d(int prec, const Line1DArgs &a, cudaStream_t st)
 {
+    if (prec == GPE_C128 && a.cluster && line1d_cluster_applies(a)) {
+        const cudaError_t e = launch_line1d_cluster(a, st);
+        if (e != cudaErrorNotSupported) return e;
+        cudaGetLastError();   // no cluster of that size fits: the one-CTA-per-line kernel
+    }
     return prec == GPE_C64 ? launch_line1d_f32(a, st) : launch_line1d_f64(a, st);
 }
 }  // namespace gpe
@@ -122,6 +127,7 @@ struct gpe_plan {
     int tile_var[3] = {0, 0, 0};            // tile shape per axis
     int tx_extra = 0;                       // GPE_OPT_TEST_STALL_COPIES
     bool generic_passes = false;            // GPE_OPT_GENERIC_PASSES
+    bool line_cluster = true;               // GPE_OPT_LINE_CLUSTER
     bool no_dither = false;                 // GPE_OPT_NO_DITHER
     // trap tables of one time level (gpe_step_real_trap), allocated on first use
     void *sched[3] = {nullptr, nullptr, nullptr};
@@ -785,6 +791,7 @@ static gpe_status step_real_dev(gpe_plan *p, void *psi, int64_t nsteps, const do
             l.g = p->g_dev;
             l.dt = p->dt;
             l.err = p->err;
+            l.cluster = p->line_cluster ? 1 : 0;
             if (p->cur_count > 0) {
                 l.inst_ptr = p->cur_ptrs;
                 l.slot_of = p->cur_slots;
@@ -812,6 +819,7 @@ static gpe_status step_real_dev(gpe_plan *p, void *psi, int64_t nsteps, const do
             l.g = p->g_dev;
             l.dt = p->dt;
             l.err = p->err;
+            l.cluster = p->line_cluster ? 1 : 0;
             if (p->cur_count > 0) {
                 l.inst_ptr = p->cur_ptrs;
                 l.slot_of = p->cur_slots;
@@ -968,6 +976,10 @@ extern "C" gpe_status gpe_plan_set_option(gpe_plan *p, int option, int64_t value
         p->no_dither = value != 0;
         return GPE_OK;
     }
+    if (option == GPE_OPT_LINE_CLUSTER) {
+        p->line_cluster = value != 0;
+        return GPE_OK;
+    }
     return fail(GPE_EINVAL, "unknown plan option");
 }
 
@@ -980,6 +992,7 @@ extern "C" gpe_status gpe_plan_get_option(const gpe_plan *p, int option, int64_t
     else if (option == GPE_OPT_TEST_STALL_COPIES) *value = p->tx_extra ? 1 : 0;
     else if (option == GPE_OPT_GENERIC_PASSES) *value = p->generic_passes ? 1 : 0;
     else if (option == GPE_OPT_NO_DITHER) *value = p->no_dither ? 1 : 0;
+    else if (option == GPE_OPT_LINE_CLUSTER) *value = p->line_cluster ? 1 : 0;
     else return fail(GPE_EINVAL, "unknown plan option");
     return GPE_OK;
 }
@@ -1254,6 +1267,8 @@ static gpe_status check_err(gpe_plan *p)
         cudaMemsetAsync(p->err, 0, sizeof(int), p->st);
         cudaStreamSynchronize(p->st);
         if (h & ERR_TMA_TIMEOUT) return fail(GPE_ETIMEOUT, "a tile copy did not complete within the wait limit");
+        if (h & ERR_CLUSTER_TIMEOUT)
+            return fail(GPE_ETIMEOUT, "an exchange between the CTAs of a cluster did not complete within the wait limit");
         return fail(GPE_ENUMERIC, "norm became zero or non-finite during imaginary time");
     }
     return GPE_OK;

@@ -96,6 +96,7 @@ struct PassArgs {
 enum : int {
     ERR_NUMERIC = 1,       // non-finite or zero norm in a renormalisation
     ERR_TMA_TIMEOUT = 2,   // a tile copy did not complete within the wait limit
+    ERR_CLUSTER_TIMEOUT = 4,   // a cluster exchange did not complete within the wait limit
 };
 
 // record the thread-local message returned by gpe_last_error()
@@ -143,8 +144,15 @@ struct Line1DArgs {
     int *err;               // set to 1 if a norm turns non-finite or zero
     void *const *inst_ptr;  // optional: instance b lives at inst_ptr[b]
     const int *slot_of;     // optional: parameter/table slot of instance b
+    int cluster;            // 1: complex128 real-time steps may take the cluster kernel
 };
 cudaError_t launch_line1d(int prec, const Line1DArgs &a, cudaStream_t st);
+// complex128 real-time steps of at most LINE_CLUSTER_MAX_BATCH lines of 64,
+// 128 or 256 points, one line per cluster of 4, 8 or 16 CTAs (line_cluster.cu);
+// cudaErrorNotSupported when the device cannot place such a cluster
+constexpr int64_t LINE_CLUSTER_MAX_BATCH = 32;
+bool line1d_cluster_applies(const Line1DArgs &a);
+cudaError_t launch_line1d_cluster(const Line1DArgs &a, cudaStream_t st);
 
 // trap tables of one time level of a time-dependent harmonic trap (diag_spec.cu):
 // for every axis a < ndim and every instance, tab[a][b*n[a] + j] = exp(-i V_a c) - 1

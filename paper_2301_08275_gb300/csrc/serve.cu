@@ -580,7 +580,7 @@ static void round_once(gpe_server *s)
         SGroup *g = pd.g;
         gpe_status st = pd.st != GPE_OK ? pd.st : synced[g];
         if (st == GPE_OK && pd.err && *pd.err)
-            st = (*pd.err & ERR_TMA_TIMEOUT) ? GPE_ETIMEOUT : GPE_ENUMERIC;
+            st = (*pd.err & (ERR_TMA_TIMEOUT | ERR_CLUSTER_TIMEOUT)) ? GPE_ETIMEOUT : GPE_ENUMERIC;
         if (pd.kind == 2) {
             for (size_t j = 0; j < pd.ms.size(); ++j) {
                 Req *r = pd.ms[j];
