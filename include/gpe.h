@@ -201,11 +201,12 @@ gpe_status gpe_spectrum(gpe_plan *plan, const void *psi_dev, unsigned kinds, dou
  *                        results differ in rounding (both agree with the
  *                        FP64 reference to about 1e-14 per step).
  *   GPE_OPT_TEST_STALL_COPIES  test hook for the failure handling: 1 makes
- *                        every copy-engine tile wait expect 16 bytes more than
- *                        its copies deliver, so the wait runs out after its
- *                        limit (about 2 s per CTA), the pass abandons its
- *                        tiles, and the next synchronising call returns
- *                        GPE_ETIMEOUT.  Results of such a launch are undefined.
+ *                        every copy-engine tile wait, and every exchange wait
+ *                        of the 1D cluster kernel, expect 16 bytes more than
+ *                        arrive, so the wait runs out after its limit (about
+ *                        2 s), the kernel abandons its work, and the next
+ *                        synchronising call returns GPE_ETIMEOUT.  Results of
+ *                        such a launch are undefined.
  * gpe_plan_set_option returns GPE_EINVAL for an unknown option or value and
  * takes effect at the next launch; gpe_plan_get_option reads one back. */
 enum gpe_option {

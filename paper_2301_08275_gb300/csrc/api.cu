@@ -94,6 +94,7 @@ struct gpe_plan {
     void *vsamp = nullptr;       // sampled potential [N] in the bulk real type, or NULL
     double *g_dev = nullptr, *gamma_dev = nullptr, *scale = nullptr, *partials = nullptr;
     double *sums = nullptr, *out6 = nullptr, *out4 = nullptr;
+    double *csum = nullptr;                  // chunk sums of the line reductions
     double *ones = nullptr;                 // [batch] of 1.0 (resets the renormalisation factors)
     int *err = nullptr;
     int64_t lines_cap = 0;
@@ -377,6 +378,11 @@ extern "C" gpe_status gpe_plan_create(const gpe_plan_desc *d, void *cuda_stream,
     PLAN_TRY(dalloc(p, (void **)&p->scale, sizeof(double) * B));
     PLAN_TRY(dalloc(p, (void **)&p->partials, sizeof(double) * NQ * p->lines_cap));
     PLAN_TRY(dalloc(p, (void **)&p->sums, sizeof(double) * NQ * B));
+    {
+        int64_t nch = 1;
+        for (int a = 0; a < d->ndim; ++a) nch = std::max(nch, reduce_chunks(p->N / p->n[a]));
+        PLAN_TRY(dalloc(p, (void **)&p->csum, sizeof(double) * NQ * B * nch));
+    }
     PLAN_TRY(dalloc(p, (void **)&p->out6, sizeof(double) * 6 * B));
     PLAN_TRY(dalloc(p, (void **)&p->out4, sizeof(double) * 4 * B));
     PLAN_TRY(dalloc(p, (void **)&p->err, sizeof(int)));
@@ -792,6 +798,7 @@ static gpe_status step_real_dev(gpe_plan *p, void *psi, int64_t nsteps, const do
             l.dt = p->dt;
             l.err = p->err;
             l.cluster = p->line_cluster ? 1 : 0;
+            l.tx_extra = p->tx_extra;
             if (p->cur_count > 0) {
                 l.inst_ptr = p->cur_ptrs;
                 l.slot_of = p->cur_slots;
@@ -820,6 +827,7 @@ static gpe_status step_real_dev(gpe_plan *p, void *psi, int64_t nsteps, const do
             l.dt = p->dt;
             l.err = p->err;
             l.cluster = p->line_cluster ? 1 : 0;
+            l.tx_extra = p->tx_extra;
             if (p->cur_count > 0) {
                 l.inst_ptr = p->cur_ptrs;
                 l.slot_of = p->cur_slots;
@@ -933,9 +941,9 @@ static gpe_status diag_dev(gpe_plan *p, const void *psi)
         k.red = RED_DIAG_K;
         GPE_TRY(run(p, k));
     }
-    cudaError_t e = launch_reduce_lines(p->partials, p->lines_cap, 0, 7, B, p->N / p->n[0], p->sums, p->st);
+    cudaError_t e = launch_reduce_lines(p->partials, p->lines_cap, 0, 7, B, p->N / p->n[0], p->csum, p->sums, p->st);
     for (int a = 1; a < p->ndim && e == cudaSuccess; ++a)
-        e = launch_reduce_lines(p->partials, p->lines_cap, 6 + a, 1, B, p->N / p->n[a], p->sums, p->st);
+        e = launch_reduce_lines(p->partials, p->lines_cap, 6 + a, 1, B, p->N / p->n[a], p->csum, p->sums, p->st);
     if (e == cudaSuccess) e = launch_finish_diag(p->sums, B, p->ndim, p->n, p->dv, p->g_dev, p->out6, p->out4, p->st);
     if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("diagnostics: ") + cudaGetErrorString(e));
     return GPE_OK;
@@ -1247,8 +1255,8 @@ static gpe_status imag_steps(gpe_plan *p, void *psi, int64_t nsteps, double targ
         x2.nl_c = 0.5 * p->dt;
         x2.red = RED_NORM;
         GPE_TRY(run(p, x2));
-        cudaError_t e = launch_reduce_lines(p->partials, p->lines_cap, 0, 1, B, p->N / p->n[0], p->sums, p->st);
-        if (e == cudaSuccess) e = launch_finish_scale(p->sums, B, p->dv, target, p->scale, p->err, p->st);
+        cudaError_t e = launch_reduce_lines(p->partials, p->lines_cap, 0, 1, B, p->N / p->n[0], p->csum, p->sums,
+                                            p->st, p->dv, target, p->scale, p->err);
         if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("renormalisation: ") + cudaGetErrorString(e));
     }
     // apply the last renormalisation

@@ -11,49 +11,68 @@ namespace gpe {
 
 // ------------------------------------------------------------------ reductions
 // sums[b*NQ + q] = sum over the lines of instance b of partials[q][line], in a
-// fixed order (strided per-thread sums, then a shared-memory tree).
-__global__ void __launch_bounds__(1024) k_reduce_lines(const double *__restrict__ partials, int64_t cap, int q0,
-                                                       int64_t lpi, double *__restrict__ sums)
+// fixed order that depends only on the number of lines: chunks of
+// REDUCE_CHUNK consecutive lines are summed by one CTA each (strided
+// per-thread sums into four accumulators, warp shuffles, one shared-memory
+// stage), then one warp per (instance, quantity) adds the chunk sums (strided
+// per lane, shuffles).  FP64 additions are slow on this GPU (one warp
+// instruction per 64 cycles per SM sub-partition): spreading them over many
+// SMs is what makes the sum fast (65536 lines: 24 us in one CTA before).
+__global__ void __launch_bounds__(256) k_reduce_chunks(const double *__restrict__ partials, int64_t cap, int q0,
+                                                       int64_t lpi, int64_t nch, double *__restrict__ csum)
 {
-    // one block per (instance, quantity): thread t adds lines t, t + 1024, ...
-    // into four interleaved accumulators (independent loads in flight), then
-    // warp shuffles and one shared-memory stage finish the sum - every step in
-    // a fixed order, so the result does not change from run to run
-    __shared__ double sh[32];
-    const int b = blockIdx.x, q = q0 + blockIdx.y, t = threadIdx.x;
-    const double *p = partials + (int64_t)q * cap + (int64_t)b * lpi;
+    __shared__ double sh[8];
+    const int64_t c = blockIdx.x, b = blockIdx.z;
+    const int q = q0 + blockIdx.y, t = threadIdx.x;
+    const int64_t first = c * REDUCE_CHUNK;
+    const int64_t n = lpi - first < REDUCE_CHUNK ? lpi - first : REDUCE_CHUNK;
+    const double *p = partials + (int64_t)q * cap + b * lpi + first;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     int64_t j = t;
-    for (; j + 3 * 1024 < lpi; j += 4 * 1024) {
+    for (; j + 3 * 256 < n; j += 4 * 256) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k] += p[j + (int64_t)k * 1024];
+        for (int k = 0; k < 4; ++k) acc[k] += p[j + (int64_t)k * 256];
     }
-    for (int k = 0; j < lpi; j += 1024, ++k) acc[k & 3] += p[j];
+    for (int k = 0; j < n; j += 256, ++k) acc[k & 3] += p[j];
     double s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((t & 31) == 0) sh[t >> 5] = s;
     __syncthreads();
-    if (t < 32) {
-        s = sh[t];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (t == 0) sums[(int64_t)b * NQ + q] = s;
+    if (t == 0) {
+        const double r = ((sh[0] + sh[1]) + (sh[2] + sh[3])) + ((sh[4] + sh[5]) + (sh[6] + sh[7]));
+        csum[(b * NQ + q) * nch + c] = r;
     }
 }
 
-// Renormalisation of the imaginary-time step: s_b = sqrt(target / (sum rho dV)).
-__global__ void k_finish_scale(const double *__restrict__ sums, int64_t batch, double dv, double target,
-                               double *__restrict__ scale, int *err)
+// One warp per (instance, quantity): sums of the chunk sums.  With scale set,
+// the sum of quantity 0 (the norm) also gives the imaginary-time
+// renormalisation factor s_b = sqrt(target / (sum rho dV)).
+__global__ void __launch_bounds__(128) k_reduce_final(const double *__restrict__ csum, int q0, int nq, int64_t batch,
+                                                      int64_t nch, double *__restrict__ sums, double dv, double target,
+                                                      double *__restrict__ scale, int *err)
 {
-    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b >= batch) return;
-    const double nrm = sums[b * NQ + 0] * dv;
-    if (!(nrm > 0.0) || !isfinite(nrm)) {
-        atomicExch(err, 1);
-        scale[b] = 1.0;
-    } else {
-        scale[b] = sqrt(target / nrm);
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= batch * nq) return;      // uniform per warp
+    const int64_t b = w / nq;
+    const int q = q0 + (int)(w % nq);
+    const double *p = csum + (b * NQ + q) * nch;
+    double s = 0.0;
+    for (int64_t j = lane; j < nch; j += 32) s += p[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        sums[b * NQ + q] = s;
+        if (scale && q == 0) {
+            const double nrm = s * dv;
+            if (!(nrm > 0.0) || !isfinite(nrm)) {
+                atomicOr(err, (int)ERR_NUMERIC);
+                scale[b] = 1.0;
+            } else {
+                scale[b] = sqrt(target / nrm);
+            }
+        }
     }
 }
 
@@ -88,19 +107,19 @@ __global__ void k_finish_diag(const double *__restrict__ sums, int64_t batch, in
     out4[4 * b + 3] = sqrt(r2);
 }
 
-cudaError_t launch_reduce_lines(const double *partials, int64_t lines_cap, int nq_first, int nq, int64_t batch,
-                                int64_t lines_per_inst, double *sums, cudaStream_t st)
-{
-    dim3 grid((unsigned)batch, (unsigned)nq);
-    k_reduce_lines<<<grid, 1024, 0, st>>>(partials, lines_cap, nq_first, lines_per_inst, sums);
-    return cudaGetLastError();
-}
+int64_t reduce_chunks(int64_t lines_per_inst) { return (lines_per_inst + REDUCE_CHUNK - 1) / REDUCE_CHUNK; }
 
-cudaError_t launch_finish_scale(const double *sums, int64_t batch, double dv, double target, double *scale,
-                                int *err, cudaStream_t st)
+cudaError_t launch_reduce_lines(const double *partials, int64_t lines_cap, int nq_first, int nq, int64_t batch,
+                                int64_t lines_per_inst, double *csum, double *sums, cudaStream_t st, double dv,
+                                double target, double *scale, int *err)
 {
-    const int nb = (int)((batch + 127) / 128);
-    k_finish_scale<<<nb, 128, 0, st>>>(sums, batch, dv, target, scale, err);
+    if (batch <= 0 || nq <= 0) return cudaSuccess;
+    const int64_t nch = reduce_chunks(lines_per_inst);
+    dim3 grid((unsigned)nch, (unsigned)nq, (unsigned)batch);
+    k_reduce_chunks<<<grid, 256, 0, st>>>(partials, lines_cap, nq_first, lines_per_inst, nch, csum);
+    const int64_t warps = batch * nq;
+    k_reduce_final<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(csum, nq_first, nq, batch, nch, sums, dv, target,
+                                                              scale, err);
     return cudaGetLastError();
 }
 

@@ -145,6 +145,7 @@ struct Line1DArgs {
     void *const *inst_ptr;  // optional: instance b lives at inst_ptr[b]
     const int *slot_of;     // optional: parameter/table slot of instance b
     int cluster;            // 1: complex128 real-time steps may take the cluster kernel
+    int tx_extra;           // test hook: bytes each cluster exchange waits for beyond what arrives
 };
 cudaError_t launch_line1d(int prec, const Line1DArgs &a, cudaStream_t st);
 // complex128 real-time steps of at most LINE_CLUSTER_MAX_BATCH lines of 64,
@@ -162,10 +163,17 @@ cudaError_t launch_trap_level(int prec, void *const *tab, int ndim, const int64_
                               const double *h, const double *gamma, double c, int64_t batch, cudaStream_t st);
 
 // reductions and spectra (diag_spec.cu)
-cudaError_t launch_reduce_lines(const double *partials, int64_t lines_cap, int nq_first, int nq,
-                                int64_t batch, int64_t lines_per_inst, double *sums, cudaStream_t st);
-cudaError_t launch_finish_scale(const double *sums, int64_t batch, double dv, double target,
-                                double *scale, int *err, cudaStream_t st);
+// sums[b*NQ + q], q in [nq_first, nq_first + nq): per-instance sums of the
+// per-line partials, in a fixed order (chunks of REDUCE_CHUNK lines, then the
+// chunk sums); csum is scratch of batch * NQ * reduce_chunks(lines_per_inst)
+// doubles.  With scale set, the q = 0 sum also gives the renormalisation
+// factor scale[b] = sqrt(target / (sum * dv)) (err |= ERR_NUMERIC and
+// scale[b] = 1 for a zero or non-finite norm).
+constexpr int64_t REDUCE_CHUNK = 4096;
+int64_t reduce_chunks(int64_t lines_per_inst);
+cudaError_t launch_reduce_lines(const double *partials, int64_t lines_cap, int nq_first, int nq, int64_t batch,
+                                int64_t lines_per_inst, double *csum, double *sums, cudaStream_t st,
+                                double dv = 0.0, double target = 0.0, double *scale = nullptr, int *err = nullptr);
 cudaError_t launch_finish_diag(const double *sums, int64_t batch, int ndim, const int64_t *n, double dv,
                                const double *g, double *out6, double *out4, cudaStream_t st);
 

@@ -254,8 +254,9 @@ __global__ void __launch_bounds__(32) k_line1d_cluster(const Line1DArgs a)
     for (int64_t st = 0; st < a.nsteps; ++st) {
         const unsigned par = (unsigned)(st & 1);
         if (lane == 0) {
-            mbar_expect_tx(&xbar[0], 256);
-            mbar_expect_tx(&xbar[1], 256);
+            // 32 lanes x 8 bytes arrive per exchange (tx_extra: failure-handling test hook)
+            mbar_expect_tx(&xbar[0], 256u + (unsigned)a.tx_extra);
+            mbar_expect_tx(&xbar[1], 256u + (unsigned)a.tx_extra);
         }
         // forward transform, step A, and the exchange to the row layout
         v = fa.dif(v);

@@ -37,7 +37,9 @@ constexpr size_t kTwBytes = 3 * kMaxN * 16;       // float4 or double2 entries
 constexpr size_t kParamOff = kTwOff + kTwBytes;        // g, gamma[3]
 constexpr size_t kSumsOff = kParamOff + 256;            // NQ doubles
 constexpr size_t kOutOff = kSumsOff + 256;              // out6, out4
-constexpr size_t kScratchBytes = kOutOff + 256;
+constexpr size_t kCsumOff = kOutOff + 256;              // chunk sums of the line reductions
+constexpr size_t kCsumBytes = (sizeof(double) * NQ * ((kMaxLines + REDUCE_CHUNK - 1) / REDUCE_CHUNK) + 255) / 256 * 256;
+constexpr size_t kScratchBytes = kCsumOff + kCsumBytes;
 static_assert(kTwOff % 256 == 0 && kParamOff % 256 == 0, "scratch regions must stay aligned");
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -210,8 +212,10 @@ extern "C" gpe_status gpe_norm_energy_noalloc(const gpe_plan_desc *d, const void
     double *sums = reinterpret_cast<double *>(base + kSumsOff);
     double *out6 = reinterpret_cast<double *>(base + kOutOff);
     double *out4 = out6 + 6;
-    NA_CUDA(launch_reduce_lines(partials, kMaxLines, 0, 7, 1, N / n[0], sums, st));
-    for (int a = 1; a < d->ndim; ++a) NA_CUDA(launch_reduce_lines(partials, kMaxLines, 6 + a, 1, 1, N / n[a], sums, st));
+    double *csum = reinterpret_cast<double *>(base + kCsumOff);
+    NA_CUDA(launch_reduce_lines(partials, kMaxLines, 0, 7, 1, N / n[0], csum, sums, st));
+    for (int a = 1; a < d->ndim; ++a)
+        NA_CUDA(launch_reduce_lines(partials, kMaxLines, 6 + a, 1, 1, N / n[a], csum, sums, st));
     NA_CUDA(launch_finish_diag(sums, 1, d->ndim, n, dv, reinterpret_cast<const double *>(base + kParamOff), out6, out4,
                                st));
     NA_CUDA(cudaMemcpyAsync(out_host, out6, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));

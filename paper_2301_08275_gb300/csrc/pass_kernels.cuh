@@ -425,6 +425,54 @@ __device__ __forceinline__ void group_sum(double (&x)[LPT], double *red, int l0,
     __syncthreads();
 }
 
+// The same tree for complex64 passes, on double-float (hi + lo) values held in
+// FP32: a double-precision add is one warp instruction per 64 cycles per SM
+// sub-partition on this GPU, so per-thread and per-line sums of float
+// quantities are accumulated with error-free FP32 transformations (TwoSum)
+// instead, to about 2^-44 relative, and converted to double once per line.
+__device__ __forceinline__ void df_acc(float &hi, float &lo, float x)
+{
+    const float s = hi + x;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (x - bb);
+    hi = s;
+}
+__device__ __forceinline__ void df_add(float &hi, float &lo, float bh, float bl)
+{
+    const float s = hi + bh;
+    const float bb = s - hi;
+    const float t = ((hi - (s - bb)) + (bh - bb)) + (lo + bl);
+    hi = s + t;
+    lo = t - (hi - s);
+}
+template <int L, int TPL, int LPT>
+__device__ __forceinline__ void group_sum_df(float (&hi)[LPT], float (&lo)[LPT], float2 *red, int l0, int tl)
+{
+#pragma unroll
+    for (int ln = 0; ln < LPT; ++ln) red[tl * L + l0 + ln] = make_float2(hi[ln], lo[ln]);
+    __syncthreads();
+#pragma unroll 1
+    for (int s = TPL / 2; s > 0; s >>= 1) {
+        if (tl < s) {
+#pragma unroll
+            for (int ln = 0; ln < LPT; ++ln) {
+                float2 u = red[tl * L + l0 + ln];
+                const float2 w = red[(tl + s) * L + l0 + ln];
+                df_add(u.x, u.y, w.x, w.y);
+                red[tl * L + l0 + ln] = u;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int ln = 0; ln < LPT; ++ln) {
+        const float2 u = red[l0 + ln];
+        hi[ln] = u.x;
+        lo[ln] = u.y;
+    }
+    __syncthreads();
+}
+
 // lines carried by each thread.  Two lines per thread (16-byte shared accesses,
 // one twiddle read for both) measured slower on the strided axes at 512^3
 // (occupancy halves at 122 registers), so each thread carries one line.
@@ -684,44 +732,109 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
                     sk[ln] += k * k * cabs2(v[ln][e]);
                 }
             }
-            double q[7][LPT];
-#pragma unroll
-            for (int ln = 0; ln < LPT; ++ln) {
+            // the per-line quantities: 0 rho, 1 x^2 rho, 2 y^2 rho, 3 z^2 rho,
+            // 4 V rho, 5 rho^2, 6 kx^2 |F_x psi|^2 (y, z, V_y + V_z are constant along the row)
+            auto line_q = [&](int ln, int k, double ls0, double lsx2, double ls4, double lsv, double lsk) {
                 const int ti = g[ln].ti;
                 const double y = a.lo[1] + (double)g[ln].c0 * a.h[1], z = a.lo[2] + (double)g[ln].c1 * a.h[2];
                 const double gx = a.gamma[3 * ti + 0], gy = a.gamma[3 * ti + 1], gz = a.gamma[3 * ti + 2];
                 const double vyz = 0.5 * gy * gy * y * y + 0.5 * gz * gz * z * z;
-                q[0][ln] = (double)s0[ln];
-                q[1][ln] = (double)sx2[ln];
-                q[2][ln] = y * y * (double)s0[ln];
-                q[3][ln] = z * z * (double)s0[ln];
-                q[4][ln] = 0.5 * gx * gx * (double)sx2[ln] + vyz * (double)s0[ln] + (double)sv[ln];
-                q[5][ln] = (double)s4[ln];
-                q[6][ln] = (double)sk[ln];
-            }
-#pragma unroll 1
-            for (int k = 0; k < 7; ++k) {
-                group_sum<L, TPL, LPT>(q[k], red, l0, tl);
+                return k == 0 ? ls0
+                       : k == 1 ? lsx2
+                       : k == 2 ? y * y * ls0
+                       : k == 3 ? z * z * ls0
+                       : k == 4 ? 0.5 * gx * gx * lsx2 + vyz * ls0 + lsv
+                       : k == 5 ? ls4
+                                : lsk;
+            };
+            if constexpr (sizeof(R) == 4) {
+                // complex64: the five row sums in double-float, the products by the
+                // row's constants in double once per row (FP64 is slow here)
+                float qh[5][LPT], ql[5][LPT];
 #pragma unroll
-                for (int ln = 0; ln < LPT; ++ln)
-                    if (tl == 0 && g[ln].valid) a.partials[(int64_t)k * a.lines_cap + g[ln].lg] = q[k][ln];
+                for (int ln = 0; ln < LPT; ++ln) {
+                    qh[0][ln] = s0[ln];
+                    qh[1][ln] = sx2[ln];
+                    qh[2][ln] = s4[ln];
+                    qh[3][ln] = sv[ln];
+                    qh[4][ln] = sk[ln];
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) ql[k][ln] = 0.0f;
+                }
+#pragma unroll
+                for (int k = 0; k < 5; ++k)
+                    group_sum_df<L, TPL, LPT>(qh[k], ql[k], reinterpret_cast<float2 *>(red), l0, tl);
+                if (tl == 0) {
+#pragma unroll
+                    for (int ln = 0; ln < LPT; ++ln) {
+                        if (!g[ln].valid) continue;
+                        const double ls0 = (double)qh[0][ln] + (double)ql[0][ln];
+                        const double lsx2 = (double)qh[1][ln] + (double)ql[1][ln];
+                        const double ls4 = (double)qh[2][ln] + (double)ql[2][ln];
+                        const double lsv = (double)qh[3][ln] + (double)ql[3][ln];
+                        const double lsk = (double)qh[4][ln] + (double)ql[4][ln];
+                        // the row's constants once (FP64 instructions are what this costs)
+                        const int ti = g[ln].ti;
+                        const double y = fma((double)g[ln].c0, a.h[1], a.lo[1]);
+                        const double z = fma((double)g[ln].c1, a.h[2], a.lo[2]);
+                        const double y2 = y * y, z2 = z * z;
+                        const double gx = a.gamma[3 * ti + 0], gy = a.gamma[3 * ti + 1], gz = a.gamma[3 * ti + 2];
+                        const double vyz = 0.5 * fma(gy * gy, y2, gz * gz * z2);
+                        double *pp = a.partials + g[ln].lg;
+                        const int64_t cap = a.lines_cap;
+                        pp[0] = ls0;
+                        pp[cap] = lsx2;
+                        pp[2 * cap] = y2 * ls0;
+                        pp[3 * cap] = z2 * ls0;
+                        pp[4 * cap] = fma(0.5 * gx * gx, lsx2, fma(vyz, ls0, lsv));
+                        pp[5 * cap] = ls4;
+                        pp[6 * cap] = lsk;
+                    }
+                }
+            } else {
+                double q[7][LPT];
+#pragma unroll
+                for (int ln = 0; ln < LPT; ++ln) {
+#pragma unroll
+                    for (int k = 0; k < 7; ++k)
+                        q[k][ln] = line_q(ln, k, (double)s0[ln], (double)sx2[ln], (double)s4[ln], (double)sv[ln],
+                                          (double)sk[ln]);
+                }
+#pragma unroll 1
+                for (int k = 0; k < 7; ++k) {
+                    group_sum<L, TPL, LPT>(q[k], red, l0, tl);
+#pragma unroll
+                    for (int ln = 0; ln < LPT; ++ln)
+                        if (tl == 0 && g[ln].valid) a.partials[(int64_t)k * a.lines_cap + g[ln].lg] = q[k][ln];
+                }
             }
         } else if (rmode == RED_DIAG_K) {
             T::template fft<-1, PING>(v, sm, PING ? scr : sm, tl, l0, tw);
             const R kf = (R)a.kf[a.axis];
-            double sk[LPT];
+            R acc[LPT];
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln) {
-                R acc = (R)0;
+                acc[ln] = (R)0;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const int i = tl + TPL * e;
                     const R k = kf * (R)(i < N / 2 ? i : i - N);
-                    acc += k * k * cabs2(v[ln][e]);
+                    acc[ln] += k * k * cabs2(v[ln][e]);
                 }
-                sk[ln] = (double)acc;
             }
-            group_sum<L, TPL, LPT>(sk, red, l0, tl);
+            double sk[LPT];
+            if constexpr (sizeof(R) == 4) {
+                float lo[LPT];
+#pragma unroll
+                for (int ln = 0; ln < LPT; ++ln) lo[ln] = 0.0f;
+                group_sum_df<L, TPL, LPT>(acc, lo, reinterpret_cast<float2 *>(red), l0, tl);
+#pragma unroll
+                for (int ln = 0; ln < LPT; ++ln) sk[ln] = (double)acc[ln] + (double)lo[ln];
+            } else {
+#pragma unroll
+                for (int ln = 0; ln < LPT; ++ln) sk[ln] = (double)acc[ln];
+                group_sum<L, TPL, LPT>(sk, red, l0, tl);
+            }
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln)
                 if (tl == 0 && g[ln].valid) a.partials[(int64_t)(6 + a.axis) * a.lines_cap + g[ln].lg] = sk[ln];
@@ -740,17 +853,32 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
             for (int ln = 0; ln < LPT; ++ln)
                 point_op<R, E, TPL>(op_post, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
             if (rmode == RED_NORM) {
-                double sn[LPT];
+                if constexpr (sizeof(R) == 4) {
+                    float nh[LPT], nl[LPT];
 #pragma unroll
-                for (int ln = 0; ln < LPT; ++ln) {
-                    sn[ln] = 0.0;
+                    for (int ln = 0; ln < LPT; ++ln) {
+                        nh[ln] = 0.0f;
+                        nl[ln] = 0.0f;
 #pragma unroll
-                    for (int e = 0; e < E; ++e) sn[ln] += (double)cabs2(v[ln][e]);
+                        for (int e = 0; e < E; ++e) df_acc(nh[ln], nl[ln], cabs2(v[ln][e]));
+                    }
+                    group_sum_df<L, TPL, LPT>(nh, nl, reinterpret_cast<float2 *>(red), l0, tl);
+#pragma unroll
+                    for (int ln = 0; ln < LPT; ++ln)
+                        if (tl == 0 && g[ln].valid) a.partials[g[ln].lg] = (double)nh[ln] + (double)nl[ln];
+                } else {
+                    double sn[LPT];
+#pragma unroll
+                    for (int ln = 0; ln < LPT; ++ln) {
+                        sn[ln] = 0.0;
+#pragma unroll
+                        for (int e = 0; e < E; ++e) sn[ln] += (double)cabs2(v[ln][e]);
+                    }
+                    group_sum<L, TPL, LPT>(sn, red, l0, tl);
+#pragma unroll
+                    for (int ln = 0; ln < LPT; ++ln)
+                        if (tl == 0 && g[ln].valid) a.partials[g[ln].lg] = sn[ln];
                 }
-                group_sum<L, TPL, LPT>(sn, red, l0, tl);
-#pragma unroll
-                for (int ln = 0; ln < LPT; ++ln)
-                    if (tl == 0 && g[ln].valid) a.partials[g[ln].lg] = sn[ln];
             }
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln) {

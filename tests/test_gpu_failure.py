@@ -44,3 +44,31 @@ def test_copy_wait_that_runs_out_is_reported_and_the_context_survives(gpe):
     assert abs(e[0][0] - 1.0) < 1e-5
     p.close()
     q.close()
+
+
+def test_cluster_exchange_wait_that_runs_out_is_reported(gpe):
+    """The 1D cluster kernel's exchange waits are bounded the same way: with
+    the hook every wait expects 16 bytes more than arrive, each CTA gives up
+    after its limit, all leave together, and GPE_ETIMEOUT is reported; the
+    context then computes correct results."""
+    import torch
+    sp = gi.CONFIG_1D
+    psi0 = gi.gaussian_1d(sp, seed=0)
+    p = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma, prec=gpe.GPE_C128)
+    assert p.get_option(gpe.GPE_OPT_LINE_CLUSTER) == 1
+    p.set_option(gpe.GPE_OPT_TEST_STALL_COPIES, 1)
+    x = torch.from_numpy(psi0.copy()).cuda()
+    p.step_real(x, 3)
+    with pytest.raises(gpe.GpeError) as ei:
+        p.norm_energy(x)
+    assert ei.value.status == 6                           # GPE_ETIMEOUT
+    p.set_option(gpe.GPE_OPT_TEST_STALL_COPIES, 0)
+    q = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma, prec=gpe.GPE_C128)
+    y = torch.from_numpy(psi0.copy()).cuda()
+    z = torch.from_numpy(psi0.copy()).cuda()
+    p.step_real(y, 5)
+    q.step_real(z, 5)
+    torch.cuda.synchronize()
+    assert torch.equal(y, z)
+    p.close()
+    q.close()
