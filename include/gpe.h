@@ -124,7 +124,12 @@ gpe_status gpe_step_real_host(gpe_plan *plan, void *psi_host, int64_t nsteps);
  * steps and stops after a chunk once |E - E_previous_check| < etol for every
  * instance (etol <= 0: never stops early), or after max_steps.  The first
  * reference energy is that of the input.  steps_done (may be NULL) receives
- * the steps taken; E_final (may be NULL) receives batch energies. */
+ * the steps taken; E_final (may be NULL) receives batch energies.  The test
+ * runs on the device after each chunk; the host enqueues chunks a window at a
+ * time (2, 4, 8, then 16 chunks) and reads the stop word once per window, and
+ * the kernels of chunks queued after the test fired do nothing, so results
+ * are those of the check that stopped the run.  A zero or non-finite norm or
+ * energy returns GPE_ENUMERIC (detected at the end of its window). */
 gpe_status gpe_step_imag(gpe_plan *plan, void *psi_dev, int64_t max_steps, double target_norm,
                          double etol, int check_every, int64_t *steps_done, double *E_final);
 
@@ -224,12 +229,14 @@ enum gpe_option {
 gpe_status gpe_plan_set_option(gpe_plan *plan, int option, int64_t value);
 gpe_status gpe_plan_get_option(const gpe_plan *plan, int option, int64_t *value);
 
-/* Autotuner (no counterpart in the paper): for every axis the plan sweeps,
- * times each tile shape (and, on y/z, each staging mode unless
- * GPE_TUNE_NO_TMA) on the state that axis's pass meets inside a real-time
- * step (psi_dev, or zeros when psi_dev is NULL, advanced through the step's
- * earlier passes; the caller's array is only read), `reps` launches per
- * candidate, and sets the options of the fastest.  Choices are remembered per
+/* Autotuner (no counterpart in the paper): for every axis the plan sweeps, in
+ * the step's order, times each tile shape (and, on y/z, each staging mode
+ * unless GPE_TUNE_NO_TMA) as whole steady real-time steps with the other axes
+ * at their current choice (from psi_dev, or zeros when psi_dev is NULL,
+ * advanced through a call's prologue; the caller's array is only read),
+ * `reps` samples per candidate taken round-robin across the candidates (a
+ * sample is one step, or several on grids whose step is shorter than about
+ * 2 ms), and keeps the candidate with the fastest sample.  Choices are remembered per
  * grid, precision and instance count for the life of the process, so later
  * plans of the same shape tune without timing.  Needs two state-sized device
  * scratch arrays for the duration of the call; synchronises the plan stream.

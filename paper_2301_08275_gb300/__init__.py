@@ -374,7 +374,7 @@ class Plan:
     def get_option(self, option):
         return gpe_plan_get_option(self._h, option)
 
-    def autotune(self, psi=None, reps=3, flags=0):
+    def autotune(self, psi=None, reps=6, flags=0):
         """Time the tile shapes / staging modes on a scratch copy of psi (a CUDA
         tensor, only read) and keep the fastest; returns the chosen options."""
         gpe_plan_autotune(self._h, self._ptr(psi) if psi is not None else 0, reps, flags)

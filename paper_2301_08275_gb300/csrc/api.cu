@@ -95,6 +95,10 @@ struct gpe_plan {
     double *g_dev = nullptr, *gamma_dev = nullptr, *scale = nullptr, *partials = nullptr;
     double *sums = nullptr, *out6 = nullptr, *out4 = nullptr;
     double *csum = nullptr;                  // chunk sums of the line reductions
+    // imaginary-time convergence on the device: [0] stop word (int), [8] steps done (int64_t)
+    unsigned char *istate = nullptr;
+    double *eprev = nullptr;                 // [batch] energies of the last check
+    const int *cur_stop = nullptr;           // set while gpe_step_imag runs: kernels check it
     double *ones = nullptr;                 // [batch] of 1.0 (resets the renormalisation factors)
     int *err = nullptr;
     int64_t lines_cap = 0;
@@ -383,6 +387,8 @@ extern "C" gpe_status gpe_plan_create(const gpe_plan_desc *d, void *cuda_stream,
         for (int a = 0; a < d->ndim; ++a) nch = std::max(nch, reduce_chunks(p->N / p->n[a]));
         PLAN_TRY(dalloc(p, (void **)&p->csum, sizeof(double) * NQ * B * nch));
     }
+    PLAN_TRY(dalloc(p, (void **)&p->istate, 16));
+    PLAN_TRY(dalloc(p, (void **)&p->eprev, sizeof(double) * B));
     PLAN_TRY(dalloc(p, (void **)&p->out6, sizeof(double) * 6 * B));
     PLAN_TRY(dalloc(p, (void **)&p->out4, sizeof(double) * 4 * B));
     PLAN_TRY(dalloc(p, (void **)&p->err, sizeof(int)));
@@ -603,6 +609,7 @@ static PassArgs make_pass(const gpe_plan *p, int axis, const void *src, void *ds
     // the end of each CTA (512^3 complex64: 2.39 ms/step with the early
     // trigger, 2.15 with the late one, 2.16 without dependent launch)
     a.pdl_early = (double)p->N * (double)batch * (p->prec == GPE_C64 ? 8.0 : 16.0) <= 64.0 * 1048576.0;
+    a.stop = p->cur_stop;
     a.scale = p->scale;
     a.partials = p->partials;
     a.lines_cap = p->lines_cap;
@@ -941,10 +948,14 @@ static gpe_status diag_dev(gpe_plan *p, const void *psi)
         k.red = RED_DIAG_K;
         GPE_TRY(run(p, k));
     }
-    cudaError_t e = launch_reduce_lines(p->partials, p->lines_cap, 0, 7, B, p->N / p->n[0], p->csum, p->sums, p->st);
+    const int *stop = p->cur_stop;
+    cudaError_t e = launch_reduce_lines(p->partials, p->lines_cap, 0, 7, B, p->N / p->n[0], p->csum, p->sums, p->st,
+                                        0.0, 0.0, nullptr, nullptr, stop);
     for (int a = 1; a < p->ndim && e == cudaSuccess; ++a)
-        e = launch_reduce_lines(p->partials, p->lines_cap, 6 + a, 1, B, p->N / p->n[a], p->csum, p->sums, p->st);
-    if (e == cudaSuccess) e = launch_finish_diag(p->sums, B, p->ndim, p->n, p->dv, p->g_dev, p->out6, p->out4, p->st);
+        e = launch_reduce_lines(p->partials, p->lines_cap, 6 + a, 1, B, p->N / p->n[a], p->csum, p->sums, p->st,
+                                0.0, 0.0, nullptr, nullptr, stop);
+    if (e == cudaSuccess)
+        e = launch_finish_diag(p->sums, B, p->ndim, p->n, p->dv, p->g_dev, p->out6, p->out4, p->st, stop);
     if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("diagnostics: ") + cudaGetErrorString(e));
     return GPE_OK;
 }
@@ -1071,11 +1082,11 @@ extern "C" gpe_status gpe_plan_autotune(gpe_plan *p, const void *psi, int reps, 
             return GPE_OK;
         }
     }
-    // Each candidate is timed on the state its pass meets inside a step: prep
-    // holds psi advanced through the step's earlier passes (prologue, then the
-    // pivot pass, then the y inverse pass in 3D), and buf gets a fresh copy of
-    // prep before every timed launch.  (The x pass in particular must see
-    // physical |psi|: its nonlinear phase takes a cheaper path for small angles.)
+    // Candidates are timed as whole steady steps on the state a step meets:
+    // prep holds psi advanced through a real-time call's prologue, and buf
+    // gets a fresh copy of prep before every timed step.  (The x pass in
+    // particular must see physical |psi|: its nonlinear phase takes a cheaper
+    // path for small angles.)
     const size_t bytes = (size_t)B * (size_t)p->N * p->csize;
     void *buf = nullptr, *prep = nullptr;
     GPE_CUDA(cudaMalloc(&buf, bytes));
@@ -1111,46 +1122,88 @@ extern "C" gpe_status gpe_plan_autotune(gpe_plan *p, const void *psi, int reps, 
         st = run(p, y);
     }
     const int piv = p->ndim - 1;
-    const int order[3] = {piv, 1, 0};   // the step's pass order (3D: z, y, x; 2D: y, x)
+    // one steady real-time step on b (state in mixed space, as prep is after
+    // the prologue): the pivot pass (F K I), y inverse (3D), x (I N F), y forward (3D)
+    auto run_step = [&](void *b) -> gpe_status {
+        GPE_TRY(run(p, steady_pass(p, piv, b, B)));
+        if (p->ndim == 3) GPE_TRY(run(p, steady_pass(p, 1, b, B)));
+        GPE_TRY(run(p, steady_pass(p, 0, b, B)));
+        if (p->ndim == 3) {
+            PassArgs yf = make_pass(p, 1, b, b, B);
+            yf.fft1 = -1;
+            GPE_TRY(run(p, yf));
+        }
+        return GPE_OK;
+    };
+    // Axes in the step's order (3D: z, y, x; 2D: y, x).  Each candidate
+    // (shape, staging) of an axis is timed as a whole step, with the other
+    // axes at their current choice, from a fresh copy of prep; candidates
+    // are taken round-robin and ranked by their fastest step.  Timing the
+    // pass alone, after the copy, favoured the 16-line 512^3 z tile, which is
+    // the slower one inside the step (0.784 against 0.759 ms: the overlap of
+    // consecutive launches differs between the shapes); summed sequential
+    // timings also let clock drift between candidates decide.
+    const int order[3] = {piv, 1, 0};
+    for (int a = 0; a < 3; ++a) {
+        p->tile_var[a] = best.var[a];
+        p->use_tma[a] = best.tma[a];
+    }
+    // steps per timed sample: about 2 ms of work, so that small grids are not
+    // timed at the resolution of the events (one 1024^2 step is ~25 us)
+    int k = 1;
+    for (int r = 0; r < 2 && st == GPE_OK; ++r) {
+        if (cudaMemcpyAsync(buf, prep, bytes, cudaMemcpyDeviceToDevice, p->st) != cudaSuccess) {
+            st = fail(GPE_ECUDA, "scratch copy failed");
+            break;
+        }
+        cudaEventRecord(e0, p->st);
+        st = run_step(buf);
+        cudaEventRecord(e1, p->st);
+        float ms = 0.f;
+        if (st == GPE_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            st = fail(GPE_ECUDA, "timing a step failed");
+        if (st == GPE_OK && r == 1) k = ms > 0.f ? (int)std::min(64.0, std::max(1.0, 2.0 / (double)ms)) : 64;
+    }
     for (int oi = 0; oi < 3 && st == GPE_OK; ++oi) {
         const int a = order[oi];
         if (oi == 1 && p->ndim != 3) continue;
-        double best_ms = 1e300;
         const int ntma = (a >= 1 && !(flags & GPE_TUNE_NO_TMA)) ? 2 : 1;
-        for (int var = 0; var < 2 && st == GPE_OK; ++var) {
-            for (int ti = 0; ti < ntma && st == GPE_OK; ++ti) {
-                p->tile_var[a] = var;
-                p->use_tma[a] = ntma == 2 && ti == 0;
-                double total = 0.0;
-                for (int r = 0; r <= reps && st == GPE_OK; ++r) {   // r = 0 warms up
-                    if (cudaMemcpyAsync(buf, prep, bytes, cudaMemcpyDeviceToDevice, p->st) != cudaSuccess) {
-                        st = fail(GPE_ECUDA, "scratch copy failed");
-                        break;
-                    }
-                    cudaEventRecord(e0, p->st);
-                    st = run(p, steady_pass(p, a, buf, B));
-                    cudaEventRecord(e1, p->st);
-                    if (st != GPE_OK) break;
-                    float ms = 0.f;
-                    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                        st = fail(GPE_ECUDA, "timing the candidate failed");
-                        break;
-                    }
-                    if (r > 0) total += ms;
+        const int ncand = 2 * ntma;
+        double cand_ms[4] = {1e300, 1e300, 1e300, 1e300};
+        for (int r = 0; r <= reps && st == GPE_OK; ++r) {       // r = 0 warms every candidate up
+            for (int c = 0; c < ncand && st == GPE_OK; ++c) {
+                p->tile_var[a] = c / ntma;
+                p->use_tma[a] = ntma == 2 && c % ntma == 0;
+                if (cudaMemcpyAsync(buf, prep, bytes, cudaMemcpyDeviceToDevice, p->st) != cudaSuccess) {
+                    st = fail(GPE_ECUDA, "scratch copy failed");
+                    break;
                 }
-                if (st == GPE_OK && total < best_ms) {
-                    best_ms = total;
-                    best.var[a] = var;
-                    best.tma[a] = p->use_tma[a];
+                // one untimed step first: the copy leaves the end of the state in
+                // L2, which the first pass after it would otherwise meet
+                st = run_step(buf);
+                if (st != GPE_OK) break;
+                cudaEventRecord(e0, p->st);
+                for (int i = 0; i < k && st == GPE_OK; ++i) st = run_step(buf);
+                cudaEventRecord(e1, p->st);
+                if (st != GPE_OK) break;
+                float ms = 0.f;
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    st = fail(GPE_ECUDA, "timing the candidate failed");
+                    break;
                 }
+                if (r > 0) cand_ms[c] = std::min(cand_ms[c], (double)ms);
             }
         }
-        // advance prep through this pass (with the chosen shape) for the next axis
-        if (st == GPE_OK && oi < 2) {
-            p->tile_var[a] = best.var[a];
-            p->use_tma[a] = best.tma[a];
-            st = run(p, steady_pass(p, a, prep, B));
+        double best_ms = 1e300;
+        for (int c = 0; c < ncand && st == GPE_OK; ++c) {
+            if (cand_ms[c] < best_ms) {
+                best_ms = cand_ms[c];
+                best.var[a] = c / ntma;
+                best.tma[a] = ntma == 2 && c % ntma == 0;
+            }
         }
+        p->tile_var[a] = best.var[a];
+        p->use_tma[a] = best.tma[a];
     }
     cudaFree(prep);
     if (e0) cudaEventDestroy(e0);
@@ -1217,6 +1270,7 @@ static gpe_status imag_steps(gpe_plan *p, void *psi, int64_t nsteps, double targ
         l.dt = p->dt;
         l.target_norm_over_dv = target / p->dv;
         l.err = p->err;
+        l.stop = p->cur_stop;
         if (p->cur_count > 0) {
             l.inst_ptr = p->cur_ptrs;
             l.slot_of = p->cur_slots;
@@ -1256,7 +1310,7 @@ static gpe_status imag_steps(gpe_plan *p, void *psi, int64_t nsteps, double targ
         x2.red = RED_NORM;
         GPE_TRY(run(p, x2));
         cudaError_t e = launch_reduce_lines(p->partials, p->lines_cap, 0, 1, B, p->N / p->n[0], p->csum, p->sums,
-                                            p->st, p->dv, target, p->scale, p->err);
+                                            p->st, p->dv, target, p->scale, p->err, p->cur_stop);
         if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("renormalisation: ") + cudaGetErrorString(e));
     }
     // apply the last renormalisation
@@ -1291,30 +1345,51 @@ extern "C" gpe_status gpe_step_imag(gpe_plan *p, void *psi, int64_t max_steps, d
     if (!(target_norm > 0.0) || !isfinite(target_norm)) return fail(GPE_EINVAL, "target_norm must be positive");
     DeviceGuard dg(p->device);
     const int64_t B = p->batch;
-    std::vector<double> eprev(B), ecur(B);
+    int *d_stop = reinterpret_cast<int *>(p->istate);
+    int64_t *d_done = reinterpret_cast<int64_t *>(p->istate + 8);
+    // first reference energies, stop word and step counter on the device
     GPE_TRY(diag_dev(p, psi));
-    GPE_TRY(copy_out(p, p->out6, 6 * (size_t)B, p->pin));
-    for (int64_t b = 0; b < B; ++b) eprev[b] = p->pin[6 * b + 4];
-    int64_t done = 0;
-    while (done < max_steps) {
-        const int64_t chunk = std::min<int64_t>(check_every, max_steps - done);
-        GPE_TRY(imag_steps(p, psi, chunk, target_norm));
-        done += chunk;
-        GPE_TRY(check_err(p));
-        GPE_TRY(diag_dev(p, psi));
-        GPE_TRY(copy_out(p, p->out6, 6 * (size_t)B, p->pin));
-        bool all = etol > 0.0;
-        for (int64_t b = 0; b < B; ++b) {
-            ecur[b] = p->pin[6 * b + 4];
-            if (!isfinite(ecur[b])) return fail(GPE_ENUMERIC, "energy became non-finite");
-            if (!(fabs(ecur[b] - eprev[b]) < etol)) all = false;
-            eprev[b] = ecur[b];
+    cudaError_t e = launch_imag_init(p->out6, p->eprev, B, d_stop, d_done, p->st);
+    if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("imaginary time: ") + cudaGetErrorString(e));
+    // Chunks of check_every steps, each followed by the diagnostics and the
+    // device-side test, are enqueued a window at a time without waiting; the
+    // host reads the stop word and step counter once per window.  Once the
+    // test has fired, the kernels of the chunks still queued see the stop
+    // word and do nothing, so the state, step count and energy are those of
+    // the check that stopped the run: the rule of a host-side loop.
+    struct StopGuard {
+        gpe_plan *p;
+        ~StopGuard() { p->cur_stop = nullptr; }
+    } guard{p};
+    p->cur_stop = d_stop;
+    unsigned char *hp = reinterpret_cast<unsigned char *>(p->pin + 6 * B);
+    int64_t queued = 0, window = 2;
+    int h_stop = 0;
+    int64_t h_done = 0;
+    while (true) {
+        for (int64_t w = 0; w < window && queued < max_steps; ++w) {
+            const int64_t chunk = std::min<int64_t>(check_every, max_steps - queued);
+            GPE_TRY(imag_steps(p, psi, chunk, target_norm));
+            GPE_TRY(diag_dev(p, psi));
+            e = launch_imag_check(p->out6, p->eprev, B, etol, chunk, d_stop, d_done, p->err, p->st);
+            if (e != cudaSuccess) return fail(GPE_ECUDA, std::string("imaginary time: ") + cudaGetErrorString(e));
+            queued += chunk;
         }
-        if (all) break;
+        GPE_CUDA(cudaMemcpyAsync(hp, p->istate, 16, cudaMemcpyDeviceToHost, p->st));
+        GPE_TRY(check_err(p));     // synchronises
+        memcpy(&h_stop, hp, sizeof(int));
+        memcpy(&h_done, hp + 8, sizeof(int64_t));
+        if (h_stop == 2) return fail(GPE_ENUMERIC, "energy or norm became non-finite or zero during imaginary time");
+        if (h_stop == 1 || queued >= max_steps) break;
+        window = std::min<int64_t>(2 * window, 16);   // longer runs: fewer round trips
     }
-    if (steps_done) *steps_done = done;
-    if (E_final)
-        for (int64_t b = 0; b < B; ++b) E_final[b] = eprev[b];
+    p->cur_stop = nullptr;
+    if (steps_done) *steps_done = h_done;
+    if (E_final) {
+        GPE_CUDA(cudaMemcpyAsync(p->pin, p->eprev, sizeof(double) * B, cudaMemcpyDeviceToHost, p->st));
+        GPE_CUDA(cudaStreamSynchronize(p->st));
+        for (int64_t b = 0; b < B; ++b) E_final[b] = p->pin[b];
+    }
     return GPE_OK;
 }
 

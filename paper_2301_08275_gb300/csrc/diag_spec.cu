@@ -19,9 +19,11 @@ namespace gpe {
 // instruction per 64 cycles per SM sub-partition): spreading them over many
 // SMs is what makes the sum fast (65536 lines: 24 us in one CTA before).
 __global__ void __launch_bounds__(256) k_reduce_chunks(const double *__restrict__ partials, int64_t cap, int q0,
-                                                       int64_t lpi, int64_t nch, double *__restrict__ csum)
+                                                       int64_t lpi, int64_t nch, double *__restrict__ csum,
+                                                       const int *stop)
 {
     __shared__ double sh[8];
+    if (stop && *reinterpret_cast<const volatile int *>(stop)) return;
     const int64_t c = blockIdx.x, b = blockIdx.z;
     const int q = q0 + blockIdx.y, t = threadIdx.x;
     const int64_t first = c * REDUCE_CHUNK;
@@ -50,8 +52,9 @@ __global__ void __launch_bounds__(256) k_reduce_chunks(const double *__restrict_
 // renormalisation factor s_b = sqrt(target / (sum rho dV)).
 __global__ void __launch_bounds__(128) k_reduce_final(const double *__restrict__ csum, int q0, int nq, int64_t batch,
                                                       int64_t nch, double *__restrict__ sums, double dv, double target,
-                                                      double *__restrict__ scale, int *err)
+                                                      double *__restrict__ scale, int *err, const int *stop)
 {
+    if (stop && *reinterpret_cast<const volatile int *>(stop)) return;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= batch * nq) return;      // uniform per warp
@@ -80,8 +83,9 @@ __global__ void __launch_bounds__(128) k_reduce_final(const double *__restrict__
 // per-instance sums of the diagnostic passes.
 __global__ void k_finish_diag(const double *__restrict__ sums, int64_t batch, int ndim, int64_t n0, int64_t n1,
                               int64_t n2, double dv, const double *__restrict__ g, double *__restrict__ out6,
-                              double *__restrict__ out4)
+                              double *__restrict__ out4, const int *stop)
 {
+    if (stop && *reinterpret_cast<const volatile int *>(stop)) return;
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= batch) return;
     const double *q = sums + b * NQ;
@@ -111,23 +115,70 @@ int64_t reduce_chunks(int64_t lines_per_inst) { return (lines_per_inst + REDUCE_
 
 cudaError_t launch_reduce_lines(const double *partials, int64_t lines_cap, int nq_first, int nq, int64_t batch,
                                 int64_t lines_per_inst, double *csum, double *sums, cudaStream_t st, double dv,
-                                double target, double *scale, int *err)
+                                double target, double *scale, int *err, const int *stop)
 {
     if (batch <= 0 || nq <= 0) return cudaSuccess;
     const int64_t nch = reduce_chunks(lines_per_inst);
     dim3 grid((unsigned)nch, (unsigned)nq, (unsigned)batch);
-    k_reduce_chunks<<<grid, 256, 0, st>>>(partials, lines_cap, nq_first, lines_per_inst, nch, csum);
+    k_reduce_chunks<<<grid, 256, 0, st>>>(partials, lines_cap, nq_first, lines_per_inst, nch, csum, stop);
     const int64_t warps = batch * nq;
     k_reduce_final<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(csum, nq_first, nq, batch, nch, sums, dv, target,
-                                                              scale, err);
+                                                              scale, err, stop);
+    return cudaGetLastError();
+}
+
+__global__ void k_imag_init(const double *__restrict__ out6, double *__restrict__ eprev, int64_t batch, int *stop,
+                            int64_t *done)
+{
+    for (int64_t b = threadIdx.x; b < batch; b += blockDim.x) eprev[b] = out6[6 * b + 4];
+    if (threadIdx.x == 0) {
+        *stop = 0;
+        *done = 0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_imag_check(const double *__restrict__ out6, double *__restrict__ eprev,
+                                                    int64_t batch, double etol, int64_t chunk, int *stop,
+                                                    int64_t *done, const int *err)
+{
+    if (*reinterpret_cast<const volatile int *>(stop)) return;
+    // the host rule of gpe_step_imag: stop when every instance moved by less
+    // than etol since the last check (never for etol <= 0)
+    int moved = !(etol > 0.0), bad = 0;
+    for (int64_t b = threadIdx.x; b < batch; b += blockDim.x) {
+        const double e = out6[6 * b + 4];
+        if (!isfinite(e)) bad = 1;
+        if (!(fabs(e - eprev[b]) < etol)) moved = 1;
+        eprev[b] = e;
+    }
+    moved = __syncthreads_or(moved);
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        *done += chunk;
+        if (bad || (err && (*reinterpret_cast<const volatile int *>(err) & ERR_NUMERIC))) *stop = 2;
+        else if (!moved) *stop = 1;
+    }
+}
+
+cudaError_t launch_imag_init(const double *out6, double *eprev, int64_t batch, int *stop, int64_t *done,
+                             cudaStream_t st)
+{
+    k_imag_init<<<1, 256, 0, st>>>(out6, eprev, batch, stop, done);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_imag_check(const double *out6, double *eprev, int64_t batch, double etol, int64_t chunk, int *stop,
+                              int64_t *done, const int *err, cudaStream_t st)
+{
+    k_imag_check<<<1, 256, 0, st>>>(out6, eprev, batch, etol, chunk, stop, done, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finish_diag(const double *sums, int64_t batch, int ndim, const int64_t *n, double dv,
-                               const double *g, double *out6, double *out4, cudaStream_t st)
+                               const double *g, double *out6, double *out4, cudaStream_t st, const int *stop)
 {
     const int nb = (int)((batch + 127) / 128);
-    k_finish_diag<<<nb, 128, 0, st>>>(sums, batch, ndim, n[0], n[1], n[2], dv, g, out6, out4);
+    k_finish_diag<<<nb, 128, 0, st>>>(sums, batch, ndim, n[0], n[1], n[2], dv, g, out6, out4, stop);
     return cudaGetLastError();
 }
 

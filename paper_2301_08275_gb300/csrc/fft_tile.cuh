@@ -383,6 +383,7 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
     using PL = typename PassPlan<N, E>::T;      // radix of each pass
     static_assert(E >= PL::radix(0) && N % E == 0, "points per thread must cover the largest radix");
     static constexpr int TPL = N / E;
+    static constexpr int LPT_ = LPT;
     static constexpr int NP = L / LPT;
     static constexpr int NT = NP * TPL;
     static constexpr int SMEM_POINTS = N * L;
@@ -554,6 +555,40 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
             fft<DIR, PING, p + 1>(v, sb, ss, tl, l0, tw);
         }
     }
+
+    // v <- conj(v) (exact).  Sweeps that run a forward and an inverse
+    // transform compute the inverse as conj(F(conj(v))) inside a two-iteration
+    // loop around one copy of the forward code (see sweep_transforms): half
+    // the instruction footprint, which matters where a CTA runs its code only
+    // once or twice per launch (grids of a few thousand lines).
+    __device__ __forceinline__ static void conj(C (&v)[LPT][E])
+    {
+#pragma unroll
+        for (int ln = 0; ln < LPT; ++ln)
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[ln][e].y = -v[ln][e].y;
+    }
 };
+
+// Two transforms with a pointwise step between them, f1, f2 in {-1 forward,
+// +1 inverse, 0 none}: one copy of the forward transform in a loop, the
+// inverse as conj(F(conj(v))).  Every kernel of the library that runs the
+// 2D/3D sweeps goes through here, so all of them round alike.
+template <typename T, bool PING, typename Mid>
+__device__ __forceinline__ void sweep_transforms(typename T::C (&v)[T::LPT_][T::E], typename T::C *sb,
+                                                 typename T::C *ss, int tl, int l0, const typename T::U *tw, int f1,
+                                                 int f2, Mid &&mid)
+{
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        const int f = h ? f2 : f1;
+        if (f != 0) {
+            if (f > 0) T::conj(v);
+            T::template fft<-1, PING>(v, sb, ss, tl, l0, tw);
+            if (f > 0) T::conj(v);
+        }
+        if (h == 0) mid();
+    }
+}
 
 }  // namespace gpe

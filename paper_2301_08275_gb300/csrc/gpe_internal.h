@@ -72,6 +72,9 @@ struct PassArgs {
     // tiles (so that waiting CTAs of the next kernel do not hold SM resources
     // while this one still has tiles to run)
     int pdl_early;
+    // device-side stop of an imaginary-time run: when set and *stop != 0 at
+    // launch, the kernel leaves without touching anything
+    const int *stop;
     const double *scale;   // per-instance renormalisation factor
     // optional indirection for batches of separately allocated instances:
     // instance b lives at inst_ptr[b] (src = dst = that pointer) and takes its
@@ -146,6 +149,7 @@ struct Line1DArgs {
     const int *slot_of;     // optional: parameter/table slot of instance b
     int cluster;            // 1: complex128 real-time steps may take the cluster kernel
     int tx_extra;           // test hook: bytes each cluster exchange waits for beyond what arrives
+    const int *stop;        // as PassArgs::stop
 };
 cudaError_t launch_line1d(int prec, const Line1DArgs &a, cudaStream_t st);
 // complex128 real-time steps of at most LINE_CLUSTER_MAX_BATCH lines of 64,
@@ -173,9 +177,22 @@ constexpr int64_t REDUCE_CHUNK = 4096;
 int64_t reduce_chunks(int64_t lines_per_inst);
 cudaError_t launch_reduce_lines(const double *partials, int64_t lines_cap, int nq_first, int nq, int64_t batch,
                                 int64_t lines_per_inst, double *csum, double *sums, cudaStream_t st,
-                                double dv = 0.0, double target = 0.0, double *scale = nullptr, int *err = nullptr);
+                                double dv = 0.0, double target = 0.0, double *scale = nullptr, int *err = nullptr,
+                                const int *stop = nullptr);
 cudaError_t launch_finish_diag(const double *sums, int64_t batch, int ndim, const int64_t *n, double dv,
-                               const double *g, double *out6, double *out4, cudaStream_t st);
+                               const double *g, double *out6, double *out4, cudaStream_t st,
+                               const int *stop = nullptr);
+// Device-side convergence test of gpe_step_imag: imag_init takes the energies
+// of out6 as the first reference and clears the stop word and step counter;
+// imag_check (after each chunk of `chunk` steps and its diagnostics), unless
+// *stop is already set, adds chunk to *done, compares every instance's energy
+// with its reference (|E - E_prev| < etol for all: *stop = 1; a non-finite
+// energy or a set ERR_NUMERIC bit in *err: *stop = 2) and makes it the new
+// reference.  The kernels of later chunks see *stop and do nothing.
+cudaError_t launch_imag_init(const double *out6, double *eprev, int64_t batch, int *stop, int64_t *done,
+                             cudaStream_t st);
+cudaError_t launch_imag_check(const double *out6, double *eprev, int64_t batch, double etol, int64_t chunk, int *stop,
+                              int64_t *done, const int *err, cudaStream_t st);
 
 struct SpecArgs {
     int prec;

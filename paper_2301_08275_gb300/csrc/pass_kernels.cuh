@@ -633,6 +633,9 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
     // visible.  Without the launch attribute it returns at once.
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
     if (a.pdl_early) asm volatile("griddepcontrol.launch_dependents;\n" :::);
+    // an imaginary-time run that has met its stopping rule: nothing to do
+    // (no copy has been issued yet; every thread reads the same word)
+    if (a.stop && *reinterpret_cast<const volatile int *>(a.stop)) return;
 
     auto stage = [&](int64_t tile, C *buf, int b) {
         if (tma) {
@@ -842,13 +845,11 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln)
                 point_op<R, E, TPL>(op_pre, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
-            if (fft1 < 0) T::template fft<-1, PING>(v, sm, PING ? scr : sm, tl, l0, tw);
-            else if (fft1 > 0) T::template fft<1, PING>(v, sm, PING ? scr : sm, tl, l0, tw);
+            sweep_transforms<T, PING>(v, sm, PING ? scr : sm, tl, l0, tw, fft1, fft2, [&]() {
 #pragma unroll
-            for (int ln = 0; ln < LPT; ++ln)
-                point_op<R, E, TPL>(op_mid, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
-            if (fft2 < 0) T::template fft<-1, PING>(v, sm, PING ? scr : sm, tl, l0, tw);
-            else if (fft2 > 0) T::template fft<1, PING>(v, sm, PING ? scr : sm, tl, l0, tw);
+                for (int ln = 0; ln < LPT; ++ln)
+                    point_op<R, E, TPL>(op_mid, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
+            });
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln)
                 point_op<R, E, TPL>(op_post, v[ln], a, g[ln].inst, g[ln].ti, g[ln].c0, g[ln].c1, tl, g[ln].off);
@@ -922,6 +923,7 @@ __global__ void __launch_bounds__(Tile<R, N, L, true>::NT) k_line1d(const Line1D
     using C = typename T::C;
     constexpr int E = T::E, TPL = T::TPL;
     using U = typename T::U;
+    if (a.stop && *reinterpret_cast<const volatile int *>(a.stop)) return;   // see k_pass
     extern __shared__ __align__(128) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
     double *red = reinterpret_cast<double *>(smraw + sizeof(C) * T::SMEM_POINTS);

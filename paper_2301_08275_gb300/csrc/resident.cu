@@ -65,11 +65,9 @@ __global__ void __launch_bounds__(ResidentCfg<N>::NT, 1) k_resident2d(const Resi
 #pragma unroll
                 for (int e = 0; e < E; ++e) v[0][e] = st[row * N + rtl + TPL * e];
                 point_op<float, E, TPL>(op_pre, v[0], *sa, 0, ti, row, 0, rtl, 0);
-                if (fft1 < 0) Rows::template fft<-1>(v, scr + rg * N, nullptr, rtl, 0, tw);
-                else if (fft1 > 0) Rows::template fft<1>(v, scr + rg * N, nullptr, rtl, 0, tw);
-                point_op<float, E, TPL>(op_mid, v[0], *sa, 0, ti, row, 0, rtl, 0);
-                if (fft2 < 0) Rows::template fft<-1>(v, scr + rg * N, nullptr, rtl, 0, tw);
-                else if (fft2 > 0) Rows::template fft<1>(v, scr + rg * N, nullptr, rtl, 0, tw);
+                sweep_transforms<Rows, false>(v, scr + rg * N, nullptr, rtl, 0, tw, fft1, fft2, [&]() {
+                    point_op<float, E, TPL>(op_mid, v[0], *sa, 0, ti, row, 0, rtl, 0);
+                });
 #pragma unroll
                 for (int e = 0; e < E; ++e) st[row * N + rtl + TPL * e] = v[0][e];
                 __syncthreads();                 // the exchange region is reused by the next rows
@@ -81,9 +79,9 @@ __global__ void __launch_bounds__(ResidentCfg<N>::NT, 1) k_resident2d(const Resi
                 C v[1][E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) v[0][e] = st[(ctl + TPL * e) * N + col];
-                Cols::template fft<-1>(v, scr, nullptr, ctl, cl, tw);
-                point_op<float, E, TPL>(OP_KREAL, v[0], *sa, 0, ti, col, 0, ctl, 0);
-                Cols::template fft<1>(v, scr, nullptr, ctl, cl, tw);
+                sweep_transforms<Cols, false>(v, scr, nullptr, ctl, cl, tw, -1, +1, [&]() {
+                    point_op<float, E, TPL>(OP_KREAL, v[0], *sa, 0, ti, col, 0, ctl, 0);
+                });
 #pragma unroll
                 for (int e = 0; e < E; ++e) st[(ctl + TPL * e) * N + col] = v[0][e];
                 __syncthreads();
