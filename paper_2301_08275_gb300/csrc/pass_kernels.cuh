@@ -445,32 +445,54 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float bh, float bl)
     hi = s + t;
     lo = t - (hi - s);
 }
+// The tree adds tl + s into tl for s = TPL/2, ..., 1, like group_sum, so
+// every tile shape adds in one order.  Thread t works on line t mod NP at
+// position tl = t div NP (NP = L / LPT): a warp holds 32/NP consecutive
+// positions of each of its lines, so the levels with s < 32/NP pair lanes of
+// one warp (lane xor s*NP) and run as shuffles; only the levels above them go
+// through shared memory and barriers.  The result is valid where tl == 0.
 template <int L, int TPL, int LPT>
 __device__ __forceinline__ void group_sum_df(float (&hi)[LPT], float (&lo)[LPT], float2 *red, int l0, int tl)
 {
+    constexpr int NP = L / LPT;
+    constexpr bool WARP = NP <= 32 && 32 % NP == 0 && (NP * TPL) % 32 == 0;   // whole warps, lines interleaved
+    constexpr int SW = WARP ? (32 / NP < TPL ? 32 / NP : TPL) : 1;            // positions of a line per warp
+    if constexpr (TPL > SW) {
 #pragma unroll
-    for (int ln = 0; ln < LPT; ++ln) red[tl * L + l0 + ln] = make_float2(hi[ln], lo[ln]);
-    __syncthreads();
+        for (int ln = 0; ln < LPT; ++ln) red[tl * L + l0 + ln] = make_float2(hi[ln], lo[ln]);
+        __syncthreads();
 #pragma unroll 1
-    for (int s = TPL / 2; s > 0; s >>= 1) {
-        if (tl < s) {
+        for (int s = TPL / 2; s >= SW; s >>= 1) {
+            if (tl < s) {
+#pragma unroll
+                for (int ln = 0; ln < LPT; ++ln) {
+                    float2 u = red[tl * L + l0 + ln];
+                    const float2 w = red[(tl + s) * L + l0 + ln];
+                    df_add(u.x, u.y, w.x, w.y);
+                    red[tl * L + l0 + ln] = u;
+                }
+            }
+            __syncthreads();
+        }
+        if (tl < SW) {
 #pragma unroll
             for (int ln = 0; ln < LPT; ++ln) {
-                float2 u = red[tl * L + l0 + ln];
-                const float2 w = red[(tl + s) * L + l0 + ln];
-                df_add(u.x, u.y, w.x, w.y);
-                red[tl * L + l0 + ln] = u;
+                const float2 u = red[tl * L + l0 + ln];
+                hi[ln] = u.x;
+                lo[ln] = u.y;
             }
         }
-        __syncthreads();
+        __syncthreads();     // the next reduction reuses red
     }
 #pragma unroll
-    for (int ln = 0; ln < LPT; ++ln) {
-        const float2 u = red[l0 + ln];
-        hi[ln] = u.x;
-        lo[ln] = u.y;
+    for (int s = SW / 2; s >= 1; s >>= 1) {
+#pragma unroll
+        for (int ln = 0; ln < LPT; ++ln) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi[ln], s * NP);
+            const float ol = __shfl_xor_sync(0xffffffffu, lo[ln], s * NP);
+            df_add(hi[ln], lo[ln], oh, ol);
+        }
     }
-    __syncthreads();
 }
 
 // lines carried by each thread.  Two lines per thread (16-byte shared accesses,
