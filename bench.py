@@ -365,7 +365,7 @@ def config_record(key, steps=None):
     dt = np.complex64 if prec == gpe.GPE_C64 else np.complex128
     x = torch.from_numpy(np.ascontiguousarray(initial_state(key, spec)).astype(dt)).cuda()
     torch.cuda.synchronize()
-    tiles = plan.autotune(x, reps=6) if spec.ndim > 1 else None
+    tiles = plan.autotune(x, reps=10) if spec.ndim > 1 else None
     w = x.clone()
     plan.step_real(w, 5)
     del w
@@ -437,7 +437,7 @@ def run_ours(args, key, wl):
             plan.set_option(opt, int(v))
         tiles = {"fixed": args.tiles}
     else:
-        tiles = plan.autotune(psi, reps=6)     # tile shapes / staging timed on this grid, before any timed region
+        tiles = plan.autotune(psi, reps=10)     # tile shapes / staging timed on this grid, before any timed region
 
     def barrier():
         if ws > 1:
@@ -794,8 +794,8 @@ def trap_record(imag_max=20000, steps=2000, warmup=3, grid=None, seed=0, stream=
     pr = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=quench, prec=gpe.GPE_C64, stream=stream)
     psi = torch.from_numpy(gi.harmonic_gaussian(sp, seed=seed, noise=0.01).astype(np.complex64)).cuda()
     torch.cuda.synchronize()
-    tiles_i = pi.autotune(psi, reps=6)
-    tiles_r = pr.autotune(psi, reps=6)
+    tiles_i = pi.autotune(psi, reps=10)
+    tiles_r = pr.autotune(psi, reps=10)
     # warm-up on copies (the timed phases start from the real initial state)
     w = psi.clone()
     pi.step_imag(w, max(3, warmup), etol=0.0, check_every=max(3, warmup))
@@ -1001,7 +1001,7 @@ def run_bao(args):
     p = gpe.Plan(sp.n, sp.lo, sp.length, g=sp.g, dt=sp.dt, gamma=sp.gamma, prec=gpe.GPE_C64, stream=stream)
     psi = torch.from_numpy(gi.bao_gaussian(sp).astype(np.complex64)).cuda()
     torch.cuda.synchronize()
-    tiles = p.autotune(psi, reps=6)
+    tiles = p.autotune(psi, reps=10)
     w = psi.clone()
     p.step_real(w, max(3, args.warmup))
     del w
