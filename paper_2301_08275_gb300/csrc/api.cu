@@ -535,7 +535,7 @@ static const char *op_tag(int op)
 static std::string pass_kind(const PassArgs &a)
 {
     std::string s = std::string(1, "xyz"[a.axis]) + std::to_string(a.nax) + ":";
-    if (a.red == RED_DIAG_X || a.red == RED_DIAG_K) return s + "diag";
+    if (a.red == RED_DIAG_X || a.red == RED_DIAG_K || a.red == RED_DIAG_XM) return s + "diag";
     std::vector<std::string> parts;
     auto add = [&](const char *t) { if (*t) parts.push_back(t); };
     add(op_tag(a.op_pre));
@@ -937,13 +937,15 @@ extern "C" gpe_status gpe_step_real_host(gpe_plan *p, void *psi_host, int64_t ns
 
 // ------------------------------------------------------------------ diagnostics
 // norm/energy/rms of psi into p->out6 / p->out4 (device), enqueued on p->st
-static gpe_status diag_dev(gpe_plan *p, const void *psi)
+// diagnostics of psi into out6/out4; kinetic = false (rms sizes only) skips the
+// transforms that the kinetic energy needs (out6 then holds no valid energies)
+static gpe_status diag_dev(gpe_plan *p, const void *psi, bool kinetic = true)
 {
     const int64_t B = active_count(p);
     PassArgs x = make_pass(p, 0, psi, nullptr, B);
-    x.red = RED_DIAG_X;
+    x.red = kinetic ? RED_DIAG_X : RED_DIAG_XM;
     GPE_TRY(run(p, x));
-    for (int a = 1; a < p->ndim; ++a) {
+    for (int a = 1; a < p->ndim && kinetic; ++a) {
         PassArgs k = make_pass(p, a, psi, nullptr, B);
         k.red = RED_DIAG_K;
         GPE_TRY(run(p, k));
@@ -951,7 +953,7 @@ static gpe_status diag_dev(gpe_plan *p, const void *psi)
     const int *stop = p->cur_stop;
     cudaError_t e = launch_reduce_lines(p->partials, p->lines_cap, 0, 7, B, p->N / p->n[0], p->csum, p->sums, p->st,
                                         0.0, 0.0, nullptr, nullptr, stop);
-    for (int a = 1; a < p->ndim && e == cudaSuccess; ++a)
+    for (int a = 1; a < p->ndim && e == cudaSuccess && kinetic; ++a)
         e = launch_reduce_lines(p->partials, p->lines_cap, 6 + a, 1, B, p->N / p->n[a], p->csum, p->sums, p->st,
                                 0.0, 0.0, nullptr, nullptr, stop);
     if (e == cudaSuccess)
@@ -1239,7 +1241,7 @@ extern "C" gpe_status gpe_rms_size(gpe_plan *p, const void *psi, double *out)
     GPE_TRY(check_psi(p, psi));
     if (!out) return fail(GPE_EINVAL, "NULL output");
     DeviceGuard dg(p->device);
-    GPE_TRY(diag_dev(p, psi));
+    GPE_TRY(diag_dev(p, psi, false));
     return copy_out(p, p->out4, 4 * (size_t)p->batch, out);
 }
 

@@ -24,6 +24,7 @@ enum PassReduce : int {
     RED_DIAG_X = 2,  // x rows: q0 sum rho, q1 sum x^2 rho, q2 sum y^2 rho, q3 sum z^2 rho,
                      //         q4 sum V rho, q5 sum rho^2, q6 sum kx^2 |F_x psi|^2 (no store)
     RED_DIAG_K = 3,  // y or z lines: q(6+axis) sum k^2 |F_axis psi|^2 (no store)
+    RED_DIAG_XM = 4, // x rows: the real-space moments of RED_DIAG_X only (q6 = 0, no transform)
 };
 
 enum { NQ = 9 };     // reduction quantities per line

@@ -726,8 +726,9 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
 #pragma unroll
                 for (int e = 0; e < E; ++e) v[ln][e] = mk((R)0, (R)0);
 
-        if (rmode == RED_DIAG_X) {
+        if (rmode == RED_DIAG_X || rmode == RED_DIAG_XM) {
             // real-space moments of rho = |psi|^2 along each row, then kx^2 |F_x psi|^2
+            // (RED_DIAG_XM, for rms sizes: the moments only)
             const R lox = (R)a.lo[0], hx = (R)a.h[0];
             const R *vsd = static_cast<const R *>(a.vsamp_diag);
             R s0[LPT], sx2[LPT], s4[LPT], sv[LPT];
@@ -744,17 +745,20 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
                     if (vsd) sv[ln] += vsd[g[ln].off + (int64_t)(tl + TPL * e) * a.estride] * rho;
                 }
             }
-            T::template fft<-1, PING>(v, sm, PING ? scr : sm, tl, l0, tw);
-            const R kf = (R)a.kf[0];
             R sk[LPT];
 #pragma unroll
-            for (int ln = 0; ln < LPT; ++ln) {
-                sk[ln] = (R)0;
+            for (int ln = 0; ln < LPT; ++ln) sk[ln] = (R)0;
+            if (rmode == RED_DIAG_X) {
+                T::template fft<-1, PING>(v, sm, PING ? scr : sm, tl, l0, tw);
+                const R kf = (R)a.kf[0];
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int i = tl + TPL * e;
-                    const R k = kf * (R)(i < N / 2 ? i : i - N);
-                    sk[ln] += k * k * cabs2(v[ln][e]);
+                for (int ln = 0; ln < LPT; ++ln) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int i = tl + TPL * e;
+                        const R k = kf * (R)(i < N / 2 ? i : i - N);
+                        sk[ln] += k * k * cabs2(v[ln][e]);
+                    }
                 }
             }
             // the per-line quantities: 0 rho, 1 x^2 rho, 2 y^2 rho, 3 z^2 rho,
