@@ -114,7 +114,11 @@ gpe_status gpe_step_real(gpe_plan *plan, void *psi_dev, int64_t nsteps);
 gpe_status gpe_step_real_trap(gpe_plan *plan, void *psi_dev, int64_t nsteps, const double *gamma_host);
 
 /* Same as gpe_step_real on a HOST buffer: copies psi in (pageable or pinned),
- * steps on the device and copies the result back.  Uses plan workspace. */
+ * steps on the device and copies the result back.  Uses plan workspace.  For
+ * one instance of at least 64 MiB in pinned host memory (2D/3D, no sampled
+ * potential) the copies go in slabs of planes of the slowest axis on a second
+ * stream and overlap the sweeps that stay inside a slab; results are the same
+ * bits either way.  Returns when psi_host holds the result. */
 gpe_status gpe_step_real_host(gpe_plan *plan, void *psi_host, int64_t nsteps);
 
 /* Imaginary-time TSSP (ground-state paragraph: t -> -i t, renormalise each

@@ -109,6 +109,9 @@ struct gpe_plan {
     int hist_blocks = 0;
     int64_t nshells = 0;
     void *host_buf = nullptr;    // device copy for gpe_step_real_host
+    // slab pipeline of gpe_step_real_host: a copy stream and one event per slab and direction
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t slab_ev[2][16] = {};
     std::vector<void *> allocs;
     // launch context for batches of separately allocated instances (serve.cu):
     // when cur_count > 0, launches cover cur_count instances found through
@@ -215,6 +218,10 @@ static void destroy(gpe_plan *p)
     for (auto e : p->event_pool) cudaEventDestroy(e);
     for (void *a : p->allocs) cudaFree(a);
     if (p->pin) cudaFreeHost(p->pin);
+    for (auto &row : p->slab_ev)
+        for (auto e : row)
+            if (e) cudaEventDestroy(e);
+    if (p->copy_st) cudaStreamDestroy(p->copy_st);
     delete p;
 }
 
@@ -922,6 +929,118 @@ extern "C" gpe_status gpe_step_real(gpe_plan *p, void *psi, int64_t nsteps)
     return step_real_dev(p, psi, nsteps);
 }
 
+// Restrict a sweep to lines [first, first + count) of its axis (a slab of the
+// grid: whole planes of the slowest axis, so the lines are consecutive and
+// every tile starts on a tile boundary).
+static void restrict_lines(const gpe_plan *p, PassArgs &a, int axis, int64_t first, int64_t count)
+{
+    const int L = pass_lines_per_tile(p->prec, axis == 0, (int)p->n[axis], p->tile_var[axis]);
+    a.line0 = first;
+    a.lines_total = first + count;
+    a.ntiles = (count + L - 1) / L;
+}
+
+// gpe_step_real_host for one instance of at least 64 MiB in pinned host
+// memory: the state moves in slabs of whole planes of the slowest axis, and
+// the sweeps that stay inside a slab (the call's first nonlinear half-step
+// with the x transform, and the forward y transform in 3D; at the end the
+// inverse y transform and the last x sweep) run on each slab as soon as it has
+// arrived / before it leaves, on the plan stream, while the copy stream moves
+// the other slabs.  Every line is computed as in step_real_dev.
+static gpe_status step_real_host_slabs(gpe_plan *p, unsigned char *host, int64_t nsteps, int S)
+{
+    const int d = p->ndim;
+    const int64_t nslow = p->n[d - 1];
+    const int64_t planes = nslow / S;
+    const size_t plane_bytes = (size_t)(p->N / nslow) * p->csize;
+    unsigned char *dev = static_cast<unsigned char *>(p->host_buf);
+    if (!p->copy_st) GPE_CUDA(cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking));
+    for (int k = 0; k < S; ++k)
+        for (int dir = 0; dir < 2; ++dir)
+            if (!p->slab_ev[dir][k]) GPE_CUDA(cudaEventCreateWithFlags(&p->slab_ev[dir][k], cudaEventDisableTiming));
+    // lines of a slab on the x axis (rows: all but x; the slowest axis slowest)
+    // and, in 3D, on the y axis (x and z; z slowest)
+    const int64_t rows_per_plane = p->N / nslow / p->n[0];
+    const int64_t ylines_per_plane = d == 3 ? p->n[0] : 0;
+    auto slab_pass = [&](PassArgs a, int axis, int k) -> gpe_status {
+        const int64_t per = axis == 0 ? rows_per_plane : ylines_per_plane;
+        restrict_lines(p, a, axis, (int64_t)k * planes * per, planes * per);
+        return run(p, a);
+    };
+    // the plan stream must not start before earlier work on psi_host's device copy ends
+    GPE_CUDA(cudaEventRecord(p->slab_ev[1][0], p->st));
+    GPE_CUDA(cudaStreamWaitEvent(p->copy_st, p->slab_ev[1][0], 0));
+    for (int k = 0; k < S; ++k) {
+        const size_t off = (size_t)k * planes * plane_bytes, len = (size_t)planes * plane_bytes;
+        GPE_CUDA(cudaMemcpyAsync(dev + off, host + off, len, cudaMemcpyHostToDevice, p->copy_st));
+        GPE_CUDA(cudaEventRecord(p->slab_ev[0][k], p->copy_st));
+    }
+    if (nsteps == 0) {
+        GPE_CUDA(cudaEventRecord(p->slab_ev[1][0], p->copy_st));
+        GPE_CUDA(cudaStreamWaitEvent(p->st, p->slab_ev[1][0], 0));
+    }
+    // prologue per slab
+    for (int k = 0; k < S && nsteps > 0; ++k) {
+        GPE_CUDA(cudaStreamWaitEvent(p->st, p->slab_ev[0][k], 0));
+        PassArgs x0 = make_pass(p, 0, dev, dev, 1);
+        x0.op_pre = OP_NREAL;
+        set_nreal(p, x0, false);
+        x0.fft1 = -1;
+        GPE_TRY(slab_pass(x0, 0, k));
+        if (d == 3) {
+            PassArgs y = make_pass(p, 1, dev, dev, 1);
+            y.fft1 = -1;
+            GPE_TRY(slab_pass(y, 1, k));
+        }
+    }
+    const int piv = d - 1;
+    const bool dither = p->prec == GPE_C64 && !p->no_dither;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        const bool last = s == nsteps - 1;
+        PassArgs kp = make_pass(p, piv, dev, dev, 1);
+        kp.fft1 = -1;
+        kp.op_mid = OP_KREAL;
+        kp.fft2 = +1;
+        const double phi = dither ? dither_angle(s) : 0.0;
+        if (dither) set_dither(kp, phi);
+        GPE_TRY(run(p, kp));
+        for (int k = 0; k < (last ? S : 1); ++k) {
+            if (d == 3) {
+                PassArgs y = make_pass(p, 1, dev, dev, 1);
+                y.fft1 = +1;
+                if (last) GPE_TRY(slab_pass(y, 1, k));
+                else GPE_TRY(run(p, y));
+            }
+            PassArgs x = make_pass(p, 0, dev, dev, 1);
+            x.fft1 = +1;
+            x.op_mid = OP_NREAL;
+            set_nreal(p, x, !last);
+            x.dphi = phi;
+            x.fft2 = last ? 0 : -1;
+            if (last) {
+                GPE_TRY(slab_pass(x, 0, k));
+                // this slab is final: copy it out while the next ones finish
+                GPE_CUDA(cudaEventRecord(p->slab_ev[1][k], p->st));
+                GPE_CUDA(cudaStreamWaitEvent(p->copy_st, p->slab_ev[1][k], 0));
+                const size_t off = (size_t)k * planes * plane_bytes, len = (size_t)planes * plane_bytes;
+                GPE_CUDA(cudaMemcpyAsync(host + off, dev + off, len, cudaMemcpyDeviceToHost, p->copy_st));
+            } else {
+                GPE_TRY(run(p, x));
+            }
+        }
+        if (d == 3 && !last) {
+            PassArgs y = make_pass(p, 1, dev, dev, 1);
+            y.fft1 = -1;
+            GPE_TRY(run(p, y));
+        }
+    }
+    if (nsteps == 0) {
+        GPE_CUDA(cudaMemcpyAsync(host, dev, (size_t)nslow * plane_bytes, cudaMemcpyDeviceToHost, p->copy_st));
+    }
+    GPE_CUDA(cudaStreamSynchronize(p->copy_st));
+    return check_err(p);
+}
+
 extern "C" gpe_status gpe_step_real_host(gpe_plan *p, void *psi_host, int64_t nsteps)
 {
     if (!p || !psi_host) return fail(GPE_EINVAL, "NULL argument");
@@ -929,6 +1048,14 @@ extern "C" gpe_status gpe_step_real_host(gpe_plan *p, void *psi_host, int64_t ns
     DeviceGuard dg(p->device);
     const size_t bytes = (size_t)p->batch * (size_t)p->N * p->csize;
     if (!p->host_buf) GPE_TRY(dalloc(p, &p->host_buf, bytes));
+    // pinned host memory of one large 2D/3D instance: pipelined slabs
+    cudaPointerAttributes at;
+    const bool pinned = cudaPointerGetAttributes(&at, psi_host) == cudaSuccess && at.type == cudaMemoryTypeHost;
+    if (!pinned) cudaGetLastError();
+    const int S = 8;
+    if (pinned && p->ndim >= 2 && p->batch == 1 && p->cur_count == 0 && !p->vsamp && bytes >= (size_t)64 << 20 &&
+        p->n[p->ndim - 1] % S == 0)
+        return step_real_host_slabs(p, static_cast<unsigned char *>(psi_host), nsteps, S);
     GPE_CUDA(cudaMemcpyAsync(p->host_buf, psi_host, bytes, cudaMemcpyHostToDevice, p->st));
     GPE_TRY(step_real_dev(p, p->host_buf, nsteps));
     GPE_CUDA(cudaMemcpyAsync(psi_host, p->host_buf, bytes, cudaMemcpyDeviceToHost, p->st));

@@ -84,6 +84,7 @@ struct PassArgs {
     const int *slot_of;
     double *partials;      // [NQ][lines_cap] per-line sums
     int64_t lines_cap;
+    int64_t line0;         // first line of the sweep (a slab of the grid): lines line0 .. lines_total - 1
     // diagnostics geometry
     const double *gamma;   // [batch][3]
     double lo[3], h[3], kf[3];   // box corner, spacing, 2 pi / len per axis

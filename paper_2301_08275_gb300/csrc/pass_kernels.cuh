@@ -382,7 +382,7 @@ template <int L>
 __device__ __forceinline__ LineGeom line_geom(const PassArgs &a, int64_t tile, int l)
 {
     LineGeom g;
-    g.lg = tile * L + l;
+    g.lg = a.line0 + tile * L + l;
     g.valid = g.lg < a.lines_total;
     g.inst = g.valid ? int(g.lg >> a.lg_lpi) : 0;
     g.ti = a.slot_of ? a.slot_of[g.inst] : g.inst;
@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
     auto stage = [&](int64_t tile, C *buf, int b) {
         if (tma) {
             if (t == 0 && tile < a.ntiles) {
-                const int64_t lg = tile * L;
+                const int64_t lg = a.line0 + tile * L;
                 const int inst = int(lg >> a.lg_lpi);
                 const int64_t li = lg & ((int64_t(1) << a.lg_lpi) - 1);
                 const int c0 = int(li & (a.o0n - 1)), c1 = int(li >> a.lg_o0);
