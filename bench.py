@@ -502,6 +502,8 @@ def run_ours(args, key, wl):
     host = torch.empty(psi.shape, dtype=cdt, pin_memory=True)
     host.copy_(psi.cpu())
     hnp = host.numpy()
+    plan.step_real_host(hnp, 1)          # warm-up: the call's device copy and copy stream are set up here
+    host.copy_(psi.cpu())
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
