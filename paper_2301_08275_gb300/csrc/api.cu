@@ -947,7 +947,20 @@ static void restrict_lines(const gpe_plan *p, PassArgs &a, int axis, int64_t fir
 // inverse y transform and the last x sweep) run on each slab as soon as it has
 // arrived / before it leaves, on the plan stream, while the copy stream moves
 // the other slabs.  Every line is computed as in step_real_dev.
+static gpe_status step_real_host_slabs_enqueue(gpe_plan *p, unsigned char *host, int64_t nsteps, int S);
 static gpe_status step_real_host_slabs(gpe_plan *p, unsigned char *host, int64_t nsteps, int S)
+{
+    const gpe_status st = step_real_host_slabs_enqueue(p, host, nsteps, S);
+    if (st != GPE_OK) {
+        // no copy into or out of the caller's buffer may outlive the call
+        if (p->copy_st) cudaStreamSynchronize(p->copy_st);
+        cudaStreamSynchronize(p->st);
+        return st;
+    }
+    GPE_CUDA(cudaStreamSynchronize(p->copy_st));
+    return check_err(p);
+}
+static gpe_status step_real_host_slabs_enqueue(gpe_plan *p, unsigned char *host, int64_t nsteps, int S)
 {
     const int d = p->ndim;
     const int64_t nslow = p->n[d - 1];
@@ -1037,8 +1050,7 @@ static gpe_status step_real_host_slabs(gpe_plan *p, unsigned char *host, int64_t
     if (nsteps == 0) {
         GPE_CUDA(cudaMemcpyAsync(host, dev, (size_t)nslow * plane_bytes, cudaMemcpyDeviceToHost, p->copy_st));
     }
-    GPE_CUDA(cudaStreamSynchronize(p->copy_st));
-    return check_err(p);
+    return GPE_OK;
 }
 
 extern "C" gpe_status gpe_step_real_host(gpe_plan *p, void *psi_host, int64_t nsteps)
@@ -1063,9 +1075,9 @@ extern "C" gpe_status gpe_step_real_host(gpe_plan *p, void *psi_host, int64_t ns
 }
 
 // ------------------------------------------------------------------ diagnostics
-// norm/energy/rms of psi into p->out6 / p->out4 (device), enqueued on p->st
-// diagnostics of psi into out6/out4; kinetic = false (rms sizes only) skips the
-// transforms that the kinetic energy needs (out6 then holds no valid energies)
+// norm/energy/rms of psi into p->out6 / p->out4 (device), enqueued on p->st;
+// kinetic = false (rms sizes only) skips the transforms that the kinetic
+// energy needs (out6 then holds no valid energies)
 static gpe_status diag_dev(gpe_plan *p, const void *psi, bool kinetic = true)
 {
     const int64_t B = active_count(p);
