@@ -234,7 +234,7 @@ gpe_status gpe_plan_set_option(gpe_plan *plan, int option, int64_t value);
 gpe_status gpe_plan_get_option(const gpe_plan *plan, int option, int64_t *value);
 
 /* Autotuner (no counterpart in the paper): for every axis the plan sweeps, in
- * the step's order and in two rounds, times each tile shape (and, on y/z, each staging mode
+ * the step's order and twice over, times each tile shape (and, on y/z, each staging mode
  * unless GPE_TUNE_NO_TMA) as whole steady real-time steps with the other axes
  * at their current choice (from psi_dev, or zeros when psi_dev is NULL,
  * advanced through a call's prologue; the caller's array is only read),

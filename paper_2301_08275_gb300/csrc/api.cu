@@ -1284,7 +1284,7 @@ extern "C" gpe_status gpe_plan_autotune(gpe_plan *p, const void *psi, int reps, 
     // the slower one inside the step (0.784 against 0.759 ms: the overlap of
     // consecutive launches differs between the shapes); summed sequential
     // timings also let clock drift between candidates decide.
-    // two rounds over the axes: a shape's speed depends on its neighbours' (the
+    // two sweeps over the axes: a shape's speed depends on its neighbours' (the
     // overlap of consecutive launches), so the axes tuned first are tuned again
     // with the others at their choice (the 512^3 z shape was picked against
     // the default y shape and lost 0.02 ms per step once y had its own)
@@ -1311,7 +1311,7 @@ extern "C" gpe_status gpe_plan_autotune(gpe_plan *p, const void *psi, int reps, 
     }
     for (int oi = 0; oi < 6 && st == GPE_OK; ++oi) {
         const int a = order[oi];
-        if (oi % 3 == 1 && p->ndim != 3) continue;     // 2D: the pivot is y, already in the round
+        if (oi % 3 == 1 && p->ndim != 3) continue;     // 2D: the pivot is y, already tuned in this sweep
         const int ntma = (a >= 1 && !(flags & GPE_TUNE_NO_TMA)) ? 2 : 1;
         const int ncand = 2 * ntma;
         double cand_ms[4] = {1e300, 1e300, 1e300, 1e300};
