@@ -704,7 +704,8 @@ static gpe_status run(gpe_plan *p, const PassArgs &a_in)
     if (p->use_tma[a.axis] && a.axis >= 1 && a.src && !a.inst_ptr && (a.dst == nullptr || a.dst == a.src)) {
         const int L = pass_lines_per_tile(p->prec, false, a.nax, var);
         const int box = a.nax < 256 ? a.nax : 256;
-        const int64_t batch = a.lines_total / (p->N / p->n[a.axis]);
+        const int64_t lpi = p->N / p->n[a.axis];
+        const int64_t batch = (a.lines_total + lpi - 1) / lpi;   // instances the sweep reaches (a slab: its own)
         if (p->n[0] % L == 0 && ((uintptr_t)a.src) % 16 == 0) {
             gpe_plan::Tmap &c = p->tmaps[a.axis];
             if (!c.ok || c.ptr != a.src || c.batch != batch || c.lines != L) {
