@@ -376,7 +376,17 @@ template <typename R, int N, int L, bool ROWS> struct Tile {
 // per line); the arithmetic of every butterfly is the same.  With 32 the
 // passes follow Radix32 (a radix-32 first pass, one exchange fewer per
 // transform for 256 to 1024 points).
-template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struct GTile {
+//
+// PAD = true (without SW) inserts one point row (L points) after every PB
+// points, PB the first pass's radix, where a row is narrower than a bank row:
+// point i of line l sits at (i + i/PB)*L + l.  The first pass's writes, PB
+// points apart in lanes with consecutive tl, then land one row apart instead
+// of on the same banks (the 8-line tile of 512 points: 4 wavefronts per
+// warp store -> 2).  The pad is free: in every access pattern of the passes
+// the point index splits into a per-thread part and a constant with disjoint
+// bits, and i/PB splits with it (no carry), so the pad folds into the
+// thread's base and the constant offsets (layout_consistent checks this).
+template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0, bool PAD = false> struct GTile {
     using C = typename CT<R>::C;
     using U = typename UT<R>::U;
     static constexpr int E = EPT ? EPT : Radix<N>::E;
@@ -391,9 +401,16 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
 
     static constexpr int QS = 128 / (L * (int)sizeof(C)) > 1 ? 128 / (L * (int)sizeof(C)) : 1;
     static constexpr int SWS = ilog2c(PL::radix(0));
-    __host__ __device__ __forceinline__ static int sidx(int i, int l)
+    static constexpr int PB = PL::radix(0);
+    static constexpr bool PADDED = PAD && !SW && QS > 1 && PL::P > 1;
+    // points of one tile buffer (the padded layout takes N/PB rows more),
+    // a whole number of KiB so that consecutive buffers stay aligned
+    static constexpr int BUF_POINTS =
+        PADDED ? (((N + N / PB) * L * (int)sizeof(C) + 1023) / 1024) * (1024 / (int)sizeof(C)) : SMEM_POINTS;
+    __host__ __device__ __forceinline__ static constexpr int sidx(int i, int l)
     {
         if constexpr (SW) return (i ^ ((i >> SWS) & (QS - 1))) * L + l;
+        if constexpr (PADDED) return (i + i / PB) * L + l;
         return i * L + l;
     }
 
@@ -401,9 +418,12 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
     // and of the first radix, the swizzle key of i depends on tl and on e only
     // through a constant, and XOR-ing it leaves TPL*e untouched: the index is
     // (tl ^ key) + TPL*e, a per-thread base plus a constant (same value as sidx).
-    __host__ __device__ __forceinline__ static int sidx_own(int tl, int e, int l)
+    __host__ __device__ __forceinline__ static constexpr int sidx_own(int tl, int e, int l)
     {
-        if constexpr (SW && TPL % QS == 0 && TPL % (1 << SWS) == 0) {
+        if constexpr (PADDED && PB % TPL == 0) {
+            // tl < TPL and TPL*e mod PB is a multiple of TPL below PB
+            return (tl + TPL * e + (TPL * e) / PB) * L + l;
+        } else if constexpr (SW && TPL % QS == 0 && TPL % (1 << SWS) == 0) {
             const int key = ((tl >> SWS) + (TPL >> SWS) * e) & (QS - 1);
             return ((tl ^ key) + TPL * e) * L + l;
         } else {
@@ -436,10 +456,43 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
     // disjoint bits (base = (j div Ns) Ns r + k with k < Ns, m < r), so do their
     // shifted copies, and the swizzle is linear over XOR on such pairs:
     // sraw(base + m Ns) = sraw(base) ^ sraw(m Ns), the second a constant.
-    template <int Ns> __host__ __device__ __forceinline__ static int sidx_out(int sb, int m, int l)
+    template <int Ns> __host__ __device__ __forceinline__ static constexpr int sidx_out(int sb, int m, int l)
     {
         if constexpr (SW) return (sb ^ sraw(m * Ns)) * L + l;
+        if constexpr (PADDED) return (sb + m * Ns + (m * Ns) / PB) * L + l;
         return (sb + m * Ns) * L + l;
+    }
+    // the per-thread part of sidx_out (base without the line interleave)
+    __host__ __device__ __forceinline__ static constexpr int sbase(int base)
+    {
+        return SW ? sraw(base) : PADDED ? base + base / PB : base;
+    }
+    // every access pattern of the passes addresses point i of line l at
+    // sidx(i, l), and the largest index fits a tile buffer
+    template <int p = 0> static constexpr bool out_consistent()
+    {
+        if constexpr (p + 1 >= PL::P) {
+            return true;      // the last pass keeps its results in registers
+        } else {
+            constexpr int r = PL::radix(p), Ns = PL::ns(p), B = E / r;
+            for (int tl = 0; tl < TPL; ++tl)
+                for (int q = 0; q < B; ++q) {
+                    const int j = tl + q * TPL, k = j & (Ns - 1);
+                    const int base = (j / Ns) * Ns * r + k;
+                    for (int m = 0; m < r; ++m)
+                        if (sidx_out<Ns>(sbase(base), m, 0) != sidx(base + m * Ns, 0)) return false;
+                }
+            return out_consistent<p + 1>();
+        }
+    }
+    static constexpr bool layout_consistent()
+    {
+        for (int tl = 0; tl < TPL; ++tl)
+            for (int e = 0; e < E; ++e)
+                if (sidx_own(tl, e, 0) != sidx(tl + TPL * e, 0)) return false;
+        int mx = 0;
+        for (int i = 0; i < N; ++i) mx = sidx(i, L - 1) > mx ? sidx(i, L - 1) : mx;
+        return mx < BUF_POINTS && out_consistent<0>();
     }
     __device__ __forceinline__ static void st_at(C *sm, int i0, const C *x)
     {
@@ -535,7 +588,7 @@ template <typename R, int N, int L, int LPT, bool SW = false, int EPT = 0> struc
                     for (int m = 0; m < r; ++m) v[ln][q + m * B] = x[ln][m];
             } else {
                 const int base = (j / Ns) * Ns * r + k;
-                const int sb = SW ? sraw(base) : base;
+                const int sb = sbase(base);
 #pragma unroll
                 for (int m = 0; m < r; ++m) {
                     C y[LPT];

@@ -529,16 +529,23 @@ template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr b
 {
     return rows_split<R, N, ROWS, VAR>();
 }
+// Strided tiles of 32 points per thread whose point rows are narrower than a
+// bank row take the padded exchange layout instead (no index arithmetic
+// added; see GTile).
+template <typename R, int N, bool ROWS> __host__ __device__ constexpr bool pass_pad()
+{
+    return !ROWS && pass_points_per_thread<R, N, ROWS>() == 32;
+}
 template <typename R, int N, bool ROWS, int VAR>
 using PassTile = GTile<R, N, pick_lines<R, N, ROWS, VAR>(), lines_per_thread<R>(), pass_swizzle<R, N, ROWS, VAR>(),
-                       pass_points_per_thread<R, N, ROWS>()>;
+                       pass_points_per_thread<R, N, ROWS>(), pass_pad<R, N, ROWS>()>;
 
 // dynamic shared memory of one CTA without the transform scratch: two staging
 // buffers, per-line reduction scratch, twiddles, two mbarriers
 template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr size_t pass_smem_base()
 {
     using T = PassTile<R, N, ROWS, VAR>;
-    return 2 * sizeof(typename T::C) * T::SMEM_POINTS + sizeof(double) * (size_t)(T::SMEM_POINTS / T::E) +
+    return 2 * sizeof(typename T::C) * T::BUF_POINTS + sizeof(double) * (size_t)(T::SMEM_POINTS / T::E) +
            sizeof(typename T::U) * N + 2 * sizeof(uint64_t);
 }
 // CTAs per SM the registers are budgeted for: 4 per SM for split rows (1024 /
@@ -562,14 +569,14 @@ template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr i
 template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr bool pass_ping()
 {
     using T = PassTile<R, N, ROWS, VAR>;
-    constexpr size_t with = pass_smem_base<R, N, ROWS, VAR>() + sizeof(typename T::C) * T::SMEM_POINTS;
+    constexpr size_t with = pass_smem_base<R, N, ROWS, VAR>() + sizeof(typename T::C) * T::BUF_POINTS;
     return T::PL::P > 1 && pass_min_blocks<R, N, ROWS, VAR>() == 1 && with + 1024 <= 227 * 1024;
 }
 template <typename R, int N, bool ROWS, int VAR> __host__ __device__ constexpr size_t pass_smem_bytes()
 {
     using T = PassTile<R, N, ROWS, VAR>;
     return pass_smem_base<R, N, ROWS, VAR>() +
-           (pass_ping<R, N, ROWS, VAR>() ? sizeof(typename T::C) * T::SMEM_POINTS : 0);
+           (pass_ping<R, N, ROWS, VAR>() ? sizeof(typename T::C) * T::BUF_POINTS : 0);
 }
 
 // Sweep programs compiled with their slots fixed: the passes of the real- and
@@ -625,9 +632,9 @@ __global__ void __launch_bounds__(PassTile<R, N, ROWS, VAR>::NT, (pass_min_block
     constexpr bool PING = pass_ping<R, N, ROWS, VAR>();
     extern __shared__ __align__(128) unsigned char smraw[];
     C *buf0 = reinterpret_cast<C *>(smraw);
-    C *buf1 = buf0 + T::SMEM_POINTS;
-    constexpr size_t tiles_bytes = (PING ? 3 : 2) * sizeof(C) * T::SMEM_POINTS;
-    C *const scr = PING ? buf1 + T::SMEM_POINTS : nullptr;
+    C *buf1 = buf0 + T::BUF_POINTS;
+    constexpr size_t tiles_bytes = (PING ? 3 : 2) * sizeof(C) * T::BUF_POINTS;
+    C *const scr = PING ? buf1 + T::BUF_POINTS : nullptr;
     double *red = reinterpret_cast<double *>(smraw + tiles_bytes);
     U *tw = reinterpret_cast<U *>(smraw + tiles_bytes + sizeof(double) * N * L / E);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smraw + tiles_bytes + sizeof(double) * N * L / E + sizeof(U) * N);
@@ -1084,6 +1091,7 @@ static cudaError_t launch_pass_p(const PassArgs &a, cudaStream_t st, const CUten
 {
     constexpr int L = pick_lines<R, N, ROWS, VAR>();
     using T = PassTile<R, N, ROWS, VAR>;
+    static_assert(T::layout_consistent(), "shared layout of the exchanges");
     static LaunchCache lc;
     static const CUtensorMap none = {};
     const size_t smem = pass_smem_bytes<R, N, ROWS, VAR>();
