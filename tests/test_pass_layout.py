@@ -7,6 +7,15 @@ the launch bounds ask for fitting that memory, the optional third region only
 on one-CTA kernels, and the sweep-program dispatch (each fixed program
 recognised from its slots, the generic flag and unknown programs falling back
 to the generic kernel).
+
+For the shared layout of the transform exchanges it checks that every access
+pattern of the passes addresses the slot the layout assigns (each point of
+the tile at its own slot, all inside a buffer), that padded buffers keep the
+copy engine's destinations aligned, and, with a model of the shared-memory
+banks, that the strided tiles of 32 points per thread take the fewest
+wavefronts their access width allows in the first pass's stores and the last
+pass's loads; the same model finds the 4-way conflict of the unpadded 8-line
+512-point layout.
 """
 import os
 import shutil
@@ -26,6 +35,65 @@ using namespace gpe;
 static int bad = 0;
 #define CHECK(c) do { if (!(c)) { printf("FAIL %s line %d (N=%d rows=%d var=%d)\n", #c, __LINE__, N, (int)ROWS, VAR); ++bad; } } while (0)
 
+// Shared-memory bank model: 32 banks of 4-byte words; a warp access of w
+// bytes per lane runs in phases of 128/w lanes (one phase per 128 bytes), and
+// a phase takes as many wavefronts as the most distinct words it touches in
+// one bank.
+static int wavefronts(const long long (&byte)[32], int w)
+{
+    const int lanes = 128 / w < 32 ? 128 / w : 32;
+    int total = 0;
+    for (int ph = 0; ph < 32; ph += lanes) {
+        int worst = 1;
+        for (int b = 0; b < 32; ++b) {
+            long long words[64];
+            int nw = 0;
+            for (int l = ph; l < ph + lanes; ++l)
+                for (int o = 0; o < w; o += 4) {
+                    const long long wd = (byte[l] + o) / 4;
+                    if (wd % 32 != b) continue;
+                    bool seen = false;
+                    for (int i = 0; i < nw; ++i) seen = seen || words[i] == wd;
+                    if (!seen) words[nw++] = wd;
+                }
+            worst = nw > worst ? nw : worst;
+        }
+        total += worst;
+    }
+    return total;
+}
+
+// largest wavefront count of any warp access in the first pass's stores
+// (Ns = 1) and in the loads of the pass after it, for tile T
+template <typename T> void exchange_wavefronts(int &st, int &ld)
+{
+    using C = typename T::C;
+    constexpr int r = T::PL::radix(0), B = T::E / r;
+    st = ld = 0;
+    for (int w0 = 0; w0 < T::NT; w0 += 32) {
+        for (int q = 0; q < B; ++q)
+            for (int m = 0; m < r; ++m) {
+                long long byte[32];
+                for (int l = 0; l < 32; ++l) {
+                    const int t = w0 + l, l0 = (t % T::NP) * T::LPT_, tl = t / T::NP;
+                    const int base = (tl + q * T::TPL) * r;
+                    byte[l] = (long long)T::template sidx_out<1>(T::sbase(base), m, l0) * sizeof(C);
+                }
+                const int f = wavefronts(byte, (int)sizeof(C));
+                st = f > st ? f : st;
+            }
+        for (int e = 0; e < T::E; ++e) {
+            long long byte[32];
+            for (int l = 0; l < 32; ++l) {
+                const int t = w0 + l, l0 = (t % T::NP) * T::LPT_, tl = t / T::NP;
+                byte[l] = (long long)T::sidx_own(tl, e, l0) * sizeof(C);
+            }
+            const int f = wavefronts(byte, (int)sizeof(C));
+            ld = f > ld ? f : ld;
+        }
+    }
+}
+
 template <typename R, int N, bool ROWS, int VAR> void shape()
 {
     constexpr size_t smem = pass_smem_bytes<R, N, ROWS, VAR>();
@@ -37,6 +105,35 @@ template <typename R, int N, bool ROWS, int VAR> void shape()
     constexpr int nt = PassTile<R, N, ROWS, VAR>::NT;
     CHECK(!ping || minb == 1);
     CHECK(nt <= 1024);
+    using T = PassTile<R, N, ROWS, VAR>;
+    CHECK(T::layout_consistent());
+    CHECK(T::BUF_POINTS >= T::SMEM_POINTS);
+    // each point of each line at its own slot
+    {
+        static bool used[1 << 16];
+        const int span = T::BUF_POINTS;
+        bool fits = span <= (1 << 16);
+        CHECK(fits);
+        if (fits) {
+            for (int i = 0; i < span; ++i) used[i] = false;
+            bool dup = false;
+            for (int i = 0; i < N; ++i)
+                for (int l = 0; l < T::SMEM_POINTS / N; ++l) {
+                    const int k = T::sidx(i, l);
+                    if (k < 0 || k >= span || used[k]) dup = true;
+                    else used[k] = true;
+                }
+            CHECK(!dup);
+        }
+    }
+    if constexpr (T::PADDED) CHECK((sizeof(typename T::C) * T::BUF_POINTS) % 1024 == 0);
+    if constexpr (pass_pad<R, N, ROWS>() && T::PL::P > 1) {
+        int st = 0, ld = 0;
+        exchange_wavefronts<T>(st, ld);
+        const int fewest = 32 * (int)sizeof(typename T::C) / 128;
+        CHECK(st == fewest);
+        CHECK(ld == fewest);
+    }
 }
 template <typename R, bool ROWS, int VAR> void shapes()
 {
@@ -48,6 +145,22 @@ int main()
 {
     shapes<float, false, 0>(); shapes<float, false, 1>(); shapes<float, true, 0>(); shapes<float, true, 1>();
     shapes<double, false, 0>(); shapes<double, false, 1>(); shapes<double, true, 0>(); shapes<double, true, 1>();
+    {
+        // the model against a known conflict: the 8-line 512-point tile in the
+        // unpadded layout takes 4 wavefronts per first-pass warp store
+        const int N = 512, VAR = 1;
+        const bool ROWS = false;
+        using Padded = PassTile<float, 512, false, 1>;
+        using Plain = GTile<float, 512, 8, 1, false, 32, false>;
+        CHECK(Padded::PADDED && Padded::SMEM_POINTS / 512 == 8);
+        int st = 0, ld = 0;
+        exchange_wavefronts<Plain>(st, ld);
+        CHECK(st == 4);
+        CHECK(ld == 2);
+        exchange_wavefronts<Padded>(st, ld);
+        CHECK(st == 2);
+        printf("model: 8-line 512-point first-pass stores, plain 4 / padded %d wavefronts\n", st);
+    }
     const int N = 0, VAR = 0;
     const bool ROWS = false;
     int seen = 0;
