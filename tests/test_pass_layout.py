@@ -94,6 +94,60 @@ template <typename T> void exchange_wavefronts(int &st, int &ld)
     }
 }
 
+// Table of the modelled wavefronts of every exchange of every tile shape
+// (worst warp access of the stores of each non-last pass and of the loads of
+// each pass after the first, against the fewest the access width allows).
+template <typename T, int p> void pass_table()
+{
+    using C = typename T::C;
+    if constexpr (p < T::PL::P) {
+        constexpr int r = T::PL::radix(p), Ns = T::PL::ns(p), B = T::E / r;
+        int st = 0, ld = 0;
+        for (int w0 = 0; w0 < T::NT; w0 += 32) {
+            if (p + 1 < T::PL::P)
+                for (int q = 0; q < B; ++q)
+                    for (int m = 0; m < r; ++m) {
+                        long long byte[32];
+                        for (int l = 0; l < 32; ++l) {
+                            const int t = (w0 + l) % T::NT, l0 = (t % T::NP) * T::LPT_, tl = t / T::NP;
+                            const int j = tl + q * T::TPL, k = j & (Ns - 1);
+                            byte[l] = (long long)T::template sidx_out<Ns>(T::sbase((j / Ns) * Ns * r + k), m, l0) *
+                                      sizeof(C);
+                        }
+                        const int f = wavefronts(byte, (int)sizeof(C));
+                        st = f > st ? f : st;
+                    }
+            if (p >= 1)
+                for (int e = 0; e < T::E; ++e) {
+                    long long byte[32];
+                    for (int l = 0; l < 32; ++l) {
+                        const int t = (w0 + l) % T::NT, l0 = (t % T::NP) * T::LPT_, tl = t / T::NP;
+                        byte[l] = (long long)T::sidx_own(tl, e, l0) * sizeof(C);
+                    }
+                    const int f = wavefronts(byte, (int)sizeof(C));
+                    ld = f > ld ? f : ld;
+                }
+        }
+        printf("  p%d r%-2d st %2d ld %2d |", p, r, st, ld);
+        pass_table<T, p + 1>();
+    }
+}
+template <typename R, int N, bool ROWS, int VAR> void table_row()
+{
+    using T = PassTile<R, N, ROWS, VAR>;
+    printf("%s %s N=%4d shape %d: %2d lines, %2d points/thread, %s, fewest %d:", sizeof(R) == 4 ? "c64 " : "c128",
+           ROWS ? "rows   " : "strided", N, VAR, T::SMEM_POINTS / N, T::E,
+           T::PADDED ? "padded " : pass_swizzle<R, N, ROWS, VAR>() ? "swizzled" : "plain  ", 32 * (int)sizeof(typename T::C) / 128);
+    pass_table<T, 0>();
+    printf("\n");
+}
+template <typename R, bool ROWS, int VAR> void table_rows()
+{
+    table_row<R, 16, ROWS, VAR>(); table_row<R, 32, ROWS, VAR>(); table_row<R, 64, ROWS, VAR>();
+    table_row<R, 128, ROWS, VAR>(); table_row<R, 256, ROWS, VAR>(); table_row<R, 512, ROWS, VAR>();
+    table_row<R, 1024, ROWS, VAR>(); table_row<R, 2048, ROWS, VAR>(); table_row<R, 4096, ROWS, VAR>();
+}
+
 template <typename R, int N, bool ROWS, int VAR> void shape()
 {
     constexpr size_t smem = pass_smem_bytes<R, N, ROWS, VAR>();
@@ -188,6 +242,9 @@ int main()
     memset(&z, 0, sizeof(z));
     CHECK(sweep_prog_of(z) == 0);       // all slots empty: no fixed program
     printf("programs %d bad %d\n", seen, bad);
+    table_rows<float, false, 0>(); table_rows<float, false, 1>(); table_rows<double, false, 0>();
+    table_rows<double, false, 1>(); table_rows<float, true, 0>(); table_rows<float, true, 1>();
+    table_rows<double, true, 0>(); table_rows<double, true, 1>();
     return bad != 0;
 }
 """
